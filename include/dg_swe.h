@@ -1,0 +1,184 @@
+/*
+ * dg_swe.h -- C ABI of the GB300 (sm_103a) discontinuous Galerkin solver for
+ * the shallow-water equations coupled to a regularized Bingham law.
+ *
+ * Method (arXiv 2301.11238): first-order system dU/dt + div F = div Q + S,
+ * E = div G (Sec. 3, Eq. shallowR2/shallowR3) with U = (h, h u) (Eq. Uterm),
+ * F (Eq. Fterm), Q = h sigma / rho (Eq. Qterm), S (Eq. Sterm) and the velocity
+ * gradient E (Eq. gradientVel); stress sigma = sigma_N + sigma_B
+ * (Eq. binghamR) with the regularizations of Sec. 4 (Eq. sigmaTwoA-C); DG weak
+ * form per element (Sec. 5, Eq. WeakForm51/52) with the HLL flux for F
+ * (Eq. HLLSolver), central fluxes for G and Q, and strong ghost-value
+ * boundary conditions (Sec. 5.2).  Unknowns are the primitive variables
+ * V = (h, u) and E (Sec. 5).
+ *
+ * Conventions
+ *  - Every call returns dg_status and never aborts or throws.  On failure the
+ *    context (if any) keeps a message readable with dg_swe_last_error().
+ *  - The library never allocates device memory.  All device storage (state,
+ *    geometry, operators, scratch) lives in one caller-provided workspace of
+ *    dg_swe_workspace_size() bytes (dg_swe_set_workspace), so a caller's
+ *    allocator (e.g. PyTorch's) owns it.  Host memory is allocated in
+ *    dg_swe_init and released in dg_swe_destroy.
+ *  - Kernels run on the stream set by dg_swe_set_stream (default stream 0).
+ *    Calls that only enqueue work return DG_OK at enqueue; device-side errors
+ *    (non-finite state) are latched in a device status word and reported by
+ *    the next synchronizing call (dg_swe_get_state, dg_swe_run, dg_swe_sync).
+ *  - Nodal layout: a field array is [field][element][node] in double
+ *    precision, nodes contiguous.  Node j of an element is the equispaced
+ *    reference node (line: r_i = -1 + 2i/p; triangle with vertices
+ *    (-1,-1), (1,-1), (-1,1): (r, s) = (-1 + 2i/p, -1 + 2j/p), j outer,
+ *    i = 0..p-j inner) mapped affinely onto the element (dg_swe_node_coords).
+ *    V fields: h, u_1[, u_2].  E fields (2D): component 2*i + j holds
+ *    E_ij = d u_j / d x_i; in 1D the single component du/dx.
+ */
+#ifndef DG_SWE_H
+#define DG_SWE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = 1,          /* invalid argument or unsupported combination     */
+  DG_ERR_CUDA = 2,         /* a CUDA runtime call failed                      */
+  DG_ERR_WORKSPACE = 3,    /* workspace missing, too small or misaligned      */
+  DG_ERR_NONFINITE = 4,    /* the state became NaN/Inf (latched on device)    */
+  DG_ERR_NEWTON = 5,       /* Newton did not converge (implicit integrator)   */
+  DG_ERR_UNSUPPORTED = 6   /* feature not available for this configuration    */
+} dg_status;
+
+typedef struct dg_swe_ctx dg_swe_ctx;
+
+#define DG_SWE_MAX_BC 8
+
+/* Boundary-condition modes (Sec. 5.2, ghost values V+ and E+ at boundary faces). */
+enum { DG_BC_COPY = 0,       /* V+ = V- (homogeneous Neumann)                          */
+       DG_BC_DIRICHLET = 1,  /* V+ = prescribed value                                  */
+       DG_BC_WALL = 2 };     /* velocity slots only: u+ = u- - 2 (u-.n) n (extension)  */
+
+/* Regularizations of the Bingham term (Sec. 4).  1-3 are the paper's;
+ * 4 and 5 are extensions the paper does not define. */
+enum { DG_REG_NONE = 0,       /* Newtonian: sigma_B = 0                                 */
+       DG_REG_SMOOTH_MAX = 1, /* Eq. sigmaTwoA/AA                                       */
+       DG_REG_LOCAL_QUAD = 2, /* Eq. sigmaTwoB; needs sigma0 = 0 or sigma0 >= 1/(2 beta) */
+       DG_REG_TANH = 3,       /* Eq. sigmaTwoC                                          */
+       DG_REG_EXP = 4,        /* 2 sigma0 (1 - exp(-m |E|)) sign E  (Papanastasiou)     */
+       DG_REG_BIVISC = 5 };   /* min(2 gamma |E|, 2 sigma0) sign E  (bi-viscosity)      */
+
+enum { DG_PREC_FP64 = 0,     /* state, fluxes and contractions in FP64                  */
+       DG_PREC_FP32 = 1 };   /* FP32 state and arithmetic; FP64 CFL and mass reductions */
+
+typedef struct {
+  int32_t mode[7];   /* per slot: V fields (h, u_1[, u_2]) then E fields     */
+  double value[7];   /* Dirichlet values per slot                            */
+} dg_swe_bc;
+
+typedef struct {
+  int32_t dim;                  /* 1 (intervals) or 2 (triangles)                        */
+  int64_t n_vertices;
+  const double *coords;         /* host, [n_vertices][dim]                               */
+  int64_t n_elements;
+  const int32_t *elem_vertices; /* host, [n_elements][dim+1]; 1D: x1 > x0; 2D: CCW       */
+  const int8_t *face_bc;        /* host, [n_elements][dim+1] or NULL (all 0): index into
+                                   params.bc used where the face has no neighbour.
+                                   Face f of a triangle joins vertices f and (f+1)%3;
+                                   face 0 of an interval is its left end, face 1 its right */
+  const double *bed;            /* host, nodal bed H [n_elements][Np] or NULL (flat)     */
+} dg_swe_mesh;
+
+typedef struct {
+  double g, rho, alpha;         /* gravity, density, plane inclination (g_c = g cos a,
+                                   g_s = g sin a; Eq. shallow2/3)                        */
+  double eta, sigma0;           /* viscosity and yield stress (Eq. bingham)              */
+  double gamma, beta, pap_m;    /* regularization parameters (Sec. 4); pap_m for DG_REG_EXP */
+  double h_floor;               /* depth floor for wave speeds and the h-weighted mass   */
+  double cfl;                   /* explicit step safety factor                           */
+  int32_t precision;            /* DG_PREC_*                                             */
+  int32_t n_bc;                 /* entries used in bc[] (>= 1)                           */
+  dg_swe_bc bc[DG_SWE_MAX_BC];
+} dg_swe_params;
+
+typedef struct {
+  int64_t steps;                /* time steps taken since the last set_state             */
+  double t;                     /* simulated time                                        */
+  double dt_last, dt_min, dt_max;
+  double mass;                  /* sum over elements of the integral of h (FP64)         */
+  double mass0;                 /* mass at set_state                                     */
+  int32_t status;               /* latched device status (dg_status value)               */
+} dg_swe_stats;
+
+/* Builds the host-side reference operators, geometry and connectivity.
+ * order p in {1,2,3}; regularization = DG_REG_*.  Copies every host input.
+ * Errors: DG_ERR_ARG for bad sizes, non-conforming or wrongly oriented meshes,
+ * boundary tags >= n_bc, or DG_REG_LOCAL_QUAD with 0 < sigma0 < 1/(2 beta). */
+dg_status dg_swe_init(const dg_swe_mesh *mesh, int order, int regularization,
+                      const dg_swe_params *params, dg_swe_ctx **out);
+
+/* Device bytes the context needs (a multiple of 256). */
+size_t dg_swe_workspace_size(const dg_swe_ctx *ctx);
+
+/* Hands the context its device workspace (256-byte aligned, >= workspace
+ * size, owned by the caller and kept alive until dg_swe_destroy) and uploads
+ * geometry and operators on the context's stream.  DG_ERR_WORKSPACE if too
+ * small or misaligned. */
+dg_status dg_swe_set_workspace(dg_swe_ctx *ctx, void *dev_ptr, size_t bytes);
+
+/* CUDA stream (cudaStream_t) for all later work; NULL = legacy default stream. */
+dg_status dg_swe_set_stream(dg_swe_ctx *ctx, void *cuda_stream);
+
+/* Physical node coordinates, host buffer [n_elements][Np][dim]. */
+dg_status dg_swe_node_coords(const dg_swe_ctx *ctx, double *xyz);
+
+/* Sizes: Np nodes per element, nV and nE fields, n_faces unique faces. */
+dg_status dg_swe_sizes(const dg_swe_ctx *ctx, int64_t *n_elements, int32_t *np,
+                       int32_t *nv, int32_t *ne, int64_t *n_faces);
+
+/* Sets the nodal state V ([nV][K][Np] doubles; device pointer if on_device,
+ * else host) and resets time, step count and the mass reference. */
+dg_status dg_swe_set_state(dg_swe_ctx *ctx, const double *V, int on_device);
+
+/* Copies the state V (and, if E is not NULL, the velocity gradient E of the
+ * last evaluated stage) out, device or host pointers; synchronizes the stream
+ * and reports a latched device error. */
+dg_status dg_swe_get_state(dg_swe_ctx *ctx, double *V, double *E, int on_device);
+
+/* One evaluation of the semi-discrete right-hand side at V_dev:
+ * E-step (Eq. WeakForm52), face fluxes once per face, volume integrals,
+ * lift and the primitive-variable mass solve <N, dU/dV N> dV/dt = -r_V
+ * (Eq. WeakForm51 with dU/dV of Appendix A).  V_dev, dVdt_dev: device
+ * [nV][K][Np] doubles; E_dev (or NULL): device [nE][K][Np].  Enqueued on the
+ * context's stream; does not touch the context state. */
+dg_status dg_swe_residual(dg_swe_ctx *ctx, const double *V_dev, double *dVdt_dev, double *E_dev);
+
+/* One explicit SSP-RK3 (Shu-Osher) step of the state.  dt > 0 uses that
+ * step; dt <= 0 computes the stable step on the device (FP64 min-reduction):
+ *   dt = min_e cfl * dx_e / ((2p+1) lam_e + (2p+1)^2 * 2 nu / dx_e),
+ * lam_e = max over nodes of |u| + sqrt(g_c max(h, h_floor)),
+ * nu = (4 eta + max d sigma_B / dE) / rho.  If dt_taken is not NULL the
+ * call synchronizes and returns the step. */
+dg_status dg_swe_step(dg_swe_ctx *ctx, double dt, double *dt_taken);
+
+/* Advances n_steps CFL-limited SSP-RK3 steps (t_end > 0 additionally stops
+ * at t_end, which requires a host sync per step and is slower).  The steps
+ * are replayed from a CUDA graph captured on first use.  Synchronizes, fills
+ * stats (may be NULL) and reports a latched device error. */
+dg_status dg_swe_run(dg_swe_ctx *ctx, int64_t n_steps, double t_end, dg_swe_stats *stats);
+
+/* Enqueues the FP64 mass reduction and synchronizes; fills stats. */
+dg_status dg_swe_sync(dg_swe_ctx *ctx, dg_swe_stats *stats);
+
+/* Number of kernel launches one dg_swe_step enqueues (for launch accounting). */
+int32_t dg_swe_launches_per_step(const dg_swe_ctx *ctx);
+
+const char *dg_swe_last_error(const dg_swe_ctx *ctx);
+void dg_swe_destroy(dg_swe_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DG_SWE_H */

@@ -1,0 +1,200 @@
+"""GB300 (sm_103a) DG solver for shallow-water flow with a regularized Bingham law.
+
+Thin Python binding of the C ABI in include/dg_swe.h: it marshals arguments
+and hands PyTorch-owned device memory (the workspace) and CUDA streams to the
+library.  Every step of the method runs in the library's CUDA kernels; if the
+library cannot be built or loaded, constructing a solver raises.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_WORKSPACE, DG_ERR_NONFINITE,  # noqa: F401
+                   DG_ERR_NEWTON, DG_ERR_UNSUPPORTED, STATUS_NAMES)
+
+PREC_FP64, PREC_FP32 = 0, 1
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def make_params(prm, bcs=None, precision=PREC_FP64):
+    """dg_swe_params from a dict with keys g, rho, alpha, eta, sigma0, gamma,
+    beta, pap_m, h_floor, cfl and a list of (modes[7], values[7]) boundary
+    descriptors."""
+    p = _lib.Params()
+    for k in ("g", "rho", "alpha", "eta", "sigma0", "gamma", "beta", "pap_m", "h_floor", "cfl"):
+        setattr(p, k, float(prm[k]))
+    p.precision = int(precision)
+    bcs = bcs if bcs else [([0] * 7, [0.0] * 7)]
+    if len(bcs) > _lib.MAX_BC:
+        raise ValueError("too many boundary descriptors")
+    p.n_bc = len(bcs)
+    for i, (modes, vals) in enumerate(bcs):
+        for s in range(7):
+            p.bc[i].mode[s] = int(modes[s])
+            p.bc[i].value[s] = float(vals[s])
+    return p
+
+
+class Solver:
+    """One DG instance (mesh, order, regularization, parameters) on cuda:0.
+
+    Arrays crossing the boundary are float64 in the [field][element][node]
+    layout of include/dg_swe.h."""
+
+    def __init__(self, dim, coords, etov, order, reg, prm, face_bc=None, bcs=None, bed=None,
+                 precision=PREC_FP64, device="cuda", stream=None, allocate=True):
+        self.L = _lib.lib()
+        self.dim, self.order, self.reg, self.precision = int(dim), int(order), int(reg), int(precision)
+        self._coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1, dim)
+        self._etov = np.ascontiguousarray(etov, dtype=np.int32)
+        self._face_bc = None if face_bc is None else np.ascontiguousarray(face_bc, dtype=np.int8)
+        self._bed = None if bed is None else np.ascontiguousarray(bed, dtype=np.float64)
+        m = _lib.Mesh()
+        m.dim = self.dim
+        m.n_vertices = self._coords.shape[0]
+        m.coords = self._coords.ctypes.data
+        m.n_elements = self._etov.shape[0]
+        m.elem_vertices = self._etov.ctypes.data
+        m.face_bc = None if self._face_bc is None else self._face_bc.ctypes.data
+        m.bed = None if self._bed is None else self._bed.ctypes.data
+        self._params = make_params(prm, bcs, precision)
+        ctx = C.c_void_p()
+        st = self.L.dg_swe_init(C.byref(m), self.order, self.reg, C.byref(self._params), C.byref(ctx))
+        self.ctx = ctx
+        if st != DG_OK:
+            msg = self.L.dg_swe_last_error(ctx).decode() if ctx.value else ""
+            if ctx.value:
+                self.L.dg_swe_destroy(ctx)
+                self.ctx = C.c_void_p()
+            raise DGError(st, msg)
+        K, np_, nv, ne, nf = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32(), C.c_int64()
+        self.L.dg_swe_sizes(self.ctx, C.byref(K), C.byref(np_), C.byref(nv), C.byref(ne), C.byref(nf))
+        self.K, self.Np, self.nV, self.nE, self.n_faces = K.value, np_.value, nv.value, ne.value, nf.value
+        self.workspace = None
+        self.stream = None
+        if allocate:
+            self.allocate(device, stream)
+
+    # -------------------------------------------------------------- setup
+    def _check(self, st):
+        if st != DG_OK:
+            raise DGError(st, self.L.dg_swe_last_error(self.ctx).decode())
+
+    def allocate(self, device="cuda", stream=None):
+        torch = _torch()
+        nbytes = int(self.L.dg_swe_workspace_size(self.ctx))
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
+        self._check(self.L.dg_swe_set_stream(self.ctx, C.c_void_p(self.stream.cuda_stream)))
+        self._check(self.L.dg_swe_set_workspace(self.ctx, C.c_void_p(self.workspace.data_ptr()), nbytes))
+
+    @property
+    def workspace_bytes(self):
+        return int(self.L.dg_swe_workspace_size(self.ctx))
+
+    def node_coords(self):
+        out = np.empty((self.K, self.Np, self.dim))
+        self._check(self.L.dg_swe_node_coords(self.ctx, out.ctypes.data))
+        return out
+
+    def launches_per_step(self):
+        return int(self.L.dg_swe_launches_per_step(self.ctx))
+
+    # -------------------------------------------------------------- state
+    def set_state(self, V):
+        """V: numpy (nV, K, Np) float64 (host) or a CUDA float64 tensor."""
+        if isinstance(V, np.ndarray):
+            V = np.ascontiguousarray(V, dtype=np.float64)
+            assert V.shape == (self.nV, self.K, self.Np)
+            self._check(self.L.dg_swe_set_state(self.ctx, V.ctypes.data, 0))
+        else:
+            torch = _torch()
+            assert V.dtype == torch.float64 and V.is_cuda and V.is_contiguous()
+            assert tuple(V.shape) == (self.nV, self.K, self.Np)
+            self._check(self.L.dg_swe_set_state(self.ctx, C.c_void_p(V.data_ptr()), 1))
+
+    def get_state(self, with_E=True):
+        V = np.empty((self.nV, self.K, self.Np))
+        E = np.empty((self.nE, self.K, self.Np)) if with_E else None
+        self._check(self.L.dg_swe_get_state(self.ctx, V.ctypes.data,
+                                            None if E is None else E.ctypes.data, 0))
+        return (V, E) if with_E else V
+
+    def get_state_device(self, V_out):
+        self._check(self.L.dg_swe_get_state(self.ctx, C.c_void_p(V_out.data_ptr()), None, 1))
+
+    # -------------------------------------------------------------- compute
+    def residual(self, V, with_E=True):
+        """dV/dt (and E) for a state; V is a CUDA float64 tensor (nV, K, Np) or
+        a numpy array (copied to the device)."""
+        torch = _torch()
+        if isinstance(V, np.ndarray):
+            V = torch.from_numpy(np.ascontiguousarray(V, dtype=np.float64)).to(self.workspace.device)
+        dV = torch.empty_like(V)
+        E = torch.empty((self.nE, self.K, self.Np), dtype=torch.float64, device=V.device) if with_E else None
+        self._check(self.L.dg_swe_residual(self.ctx, C.c_void_p(V.data_ptr()), C.c_void_p(dV.data_ptr()),
+                                           None if E is None else C.c_void_p(E.data_ptr())))
+        return (dV, E) if with_E else dV
+
+    def step(self, dt=0.0, sync=True):
+        if sync:
+            out = C.c_double()
+            self._check(self.L.dg_swe_step(self.ctx, float(dt), C.byref(out)))
+            return out.value
+        self._check(self.L.dg_swe_step(self.ctx, float(dt), None))
+        return None
+
+    def run(self, n_steps):
+        st = _lib.Stats()
+        self._check(self.L.dg_swe_run(self.ctx, int(n_steps), 0.0, C.byref(st)))
+        return _stats_dict(st)
+
+    def sync(self):
+        st = _lib.Stats()
+        self._check(self.L.dg_swe_sync(self.ctx, C.byref(st)))
+        return _stats_dict(st)
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.L.dg_swe_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stats_dict(st):
+    return dict(steps=st.steps, t=st.t, dt_last=st.dt_last, dt_min=st.dt_min, dt_max=st.dt_max,
+                mass=st.mass, mass0=st.mass0, status=st.status)
+
+
+def solver_from_case(case, precision=PREC_FP64, order=None, with_state=True, stream=None):
+    """Build a Solver for a synthetic case; sets the initial state sampled at
+    the library's own node coordinates."""
+    p = case.order if order is None else order
+    s = Solver(case.dim, case.coords, case.etov, p, case.params["reg"], case.params,
+               face_bc=case.face_bc, bcs=case.bcs, bed=None, precision=precision, allocate=False)
+    xyz = s.node_coords()
+    V0, bed = case.initial_state(xyz)
+    if case.bed_fn is not None:
+        s.close()
+        s = Solver(case.dim, case.coords, case.etov, p, case.params["reg"], case.params,
+                   face_bc=case.face_bc, bcs=case.bcs, bed=bed, precision=precision, allocate=False)
+    s.allocate(stream=stream)
+    if with_state:
+        s.set_state(V0)
+    return s, V0, bed

@@ -1,0 +1,760 @@
+// Device kernels of the DG shallow-water / regularized-Bingham hot path.
+//
+// One explicit stage is three launches:
+//   estep_kernel   E = grad u in the weak sense of Eq. WeakForm52, written in
+//                  the equivalent strong nodal form E = grad u + LIFT(n [u]/2)
+//                  (exact for the E space of degree p); neighbour traces come
+//                  through the face-to-node map (one thread per element).
+//   face_kernel    the numerical flux once per face point: HLL for F
+//                  (Eq. HLLSolver, rotated to the face normal) minus the
+//                  central flux of Q (Sec. 5), weighted by the edge quadrature
+//                  weight and face Jacobian (one thread per face point).
+//   volume_kernel  volume integrals of Eq. WeakForm51 (flux, stress, slope and
+//                  bed source), lift of the face fluxes, the primitive-variable
+//                  mass solve M dh/dt = -r_h, M_h du/dt = -r_u - M_u dh/dt
+//                  (dU/dV of Appendix A) with a per-element Cholesky
+//                  factorization, and the SSP-RK3 stage update (one thread per
+//                  element).
+// plus FP64 reductions for the stable step and the mass integral.
+//
+// Storage is [field][element][node] (nodes contiguous), R = double or float.
+// Reference operators are passed by value as kernel parameters: with the
+// loops unrolled every thread of a warp reads the same entry, a broadcast
+// from the constant bank.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dgswe {
+
+template <int DIM, int P>
+struct Sh {
+  static constexpr int NP = DIM == 1 ? P + 1 : (P + 1) * (P + 2) / 2;
+  static constexpr int NQ1 = (3 * P + 1) / 2;
+  static constexpr int NQ = DIM == 1 ? NQ1 : NQ1 * NQ1;
+  static constexpr int NF = DIM + 1;
+  static constexpr int NFP = DIM == 1 ? 1 : P + 1;
+  static constexpr int NFQ = DIM == 1 ? 1 : (3 * P + 2) / 2;
+  static constexpr int NV = DIM + 1;
+  static constexpr int NE = DIM * DIM;
+};
+
+template <typename R>
+struct Phys {
+  R gc, gs, rho_inv, eta, sigma0, gamma, beta, pap_m, h_floor;
+  int reg;
+  int bc_mode[8][7];
+  R bc_val[8][7];
+};
+
+template <int DIM, int P, typename R>
+struct EstepOps {
+  using S = Sh<DIM, P>;
+  R Dr[S::NP * S::NP];
+  R Ds[S::NP * S::NP];
+  R LIFT[S::NP * S::NF * S::NFP];
+  int8_t fmask[S::NF * S::NFP];
+};
+
+template <int DIM, int P, typename R>
+struct FaceOps {
+  using S = Sh<DIM, P>;
+  R Lf[S::NFQ * S::NFP];
+  R wf[S::NFQ];
+  int8_t fmask[S::NF * S::NFP];
+};
+
+template <int DIM, int P, typename R>
+struct VolOps {
+  using S = Sh<DIM, P>;
+  R Vq[S::NQ * S::NP];   // l_a(q)
+  R Wr[S::NQ * S::NP];   // w_q dl_a/dr (q)
+  R Ws[S::NQ * S::NP];   // w_q dl_a/ds (q)
+  R Drq[S::NQ * S::NP];  // dl_a/dr (q) (bed gradient)
+  R Dsq[S::NQ * S::NP];
+  R wq[S::NQ];
+  R Minv[S::NP * S::NP];
+  R LfT[S::NFP * S::NFQ];  // Lf transposed: lift of face-point values to face nodes
+  int8_t fmask[S::NF * S::NFP];
+};
+
+struct DevScalars {
+  double dt, t, dt_min, dt_max, mass, mass0;
+  long long steps;
+  int status;
+  int pad;
+};
+
+// ------------------------------------------------------------------ physics
+
+// phi_k(s) / (2 s) for s >= 0 (limit phi_k'(0)/2 at s = 0): the Bingham
+// coefficient of sigma_B = (phi(s)/(2s)) (D + tr D I), s = ||D||_c / sqrt(2).
+template <typename R>
+__device__ __forceinline__ R bingham_coef(R s, const Phys<R>& ph) {
+  const R s0 = ph.sigma0, g = ph.gamma;
+  if (ph.reg == 0 || s0 == R(0)) return R(0);
+  switch (ph.reg) {
+    case 1: {  // smooth max, Eq. sigmaTwoA/AA
+      R e = R(0.5) / ph.beta;
+      R x = g * s - s0;
+      R mb = x >= e ? x : (x <= -e ? R(0) : R(0.5) * ph.beta * (x + e) * (x + e));
+      return s0 * g / (mb + s0);
+    }
+    case 2: {  // local quadratic, Eq. sigmaTwoB
+      R e = R(0.5) / ph.beta;
+      R x = g * s;
+      if (x >= s0 + e) return s0 / s;
+      if (x <= s0 - e) return g;
+      R d = s0 - x + e;
+      return (R(2) * s0 - ph.beta * d * d) / (R(2) * s);
+    }
+    case 3: {  // tanh, Eq. sigmaTwoC
+      R x = g * s;
+      if (x < R(1e-8)) return s0 * g * (R(1) - x * x / R(3));
+      return s0 * tanh(x) / s;
+    }
+    case 4: {  // exponential (extension)
+      R x = ph.pap_m * s;
+      if (x < R(1e-12)) return s0 * ph.pap_m * (R(1) - R(0.5) * x);
+      return -s0 * expm1(-x) / s;
+    }
+    case 5: {  // bi-viscosity (extension)
+      R x = g * s;
+      return x < s0 ? g : s0 / s;
+    }
+  }
+  return R(0);
+}
+
+// sigma from E (component 2i+j = du_j/dx_i); returns sig[i][j].
+template <int DIM, typename R>
+__device__ __forceinline__ void stress(const R* E, const Phys<R>& ph, R sig[DIM][DIM]) {
+  if constexpr (DIM == 1) {
+    R e = E[0];
+    R mu = R(2) * ph.eta + bingham_coef<R>(fabs(e), ph);
+    sig[0][0] = mu * R(2) * e;
+  } else {
+    R d11 = E[0], d22 = E[3], d12 = R(0.5) * (E[1] + E[2]);
+    R tr = d11 + d22;
+    R nc2 = d11 * d11 + R(2) * d12 * d12 + d22 * d22 + tr * tr;
+    R s = sqrt(R(0.5) * nc2);
+    R mu = R(2) * ph.eta + bingham_coef<R>(s, ph);
+    sig[0][0] = mu * (d11 + tr);
+    sig[1][1] = mu * (d22 + tr);
+    sig[0][1] = mu * d12;
+    sig[1][0] = mu * d12;
+  }
+}
+
+// Exterior state at a boundary face point (Sec. 5.2 ghost values).
+template <int DIM, typename R>
+__device__ __forceinline__ void ghost_V(const R* Vm, const R* n, int bc, const Phys<R>& ph, R* Vp) {
+  bool wall = false;
+#pragma unroll
+  for (int v = 0; v < DIM + 1; ++v) {
+    int md = ph.bc_mode[bc][v];
+    Vp[v] = md == 1 ? ph.bc_val[bc][v] : Vm[v];
+    if (v > 0 && md == 2) wall = true;
+  }
+  if (wall) {
+    R un = R(0);
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) un += Vm[1 + j] * n[j];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) Vp[1 + j] = Vm[1 + j] - R(2) * un * n[j];
+  }
+}
+
+template <int DIM, typename R>
+__device__ __forceinline__ void ghost_E(const R* Em, int bc, const Phys<R>& ph, R* Ep) {
+#pragma unroll
+  for (int c = 0; c < DIM * DIM; ++c) {
+    int slot = DIM + 1 + c;
+    Ep[c] = ph.bc_mode[bc][slot] == 1 ? ph.bc_val[bc][slot] : Em[c];
+  }
+}
+
+// HLL normal flux (Eq. HLLSolver in the face-normal frame; wave speeds with
+// sqrt(g_c max(h, h_floor))).
+template <int DIM, typename R>
+__device__ __forceinline__ void hll(const R* Vm, const R* Vp, const R* n, const Phys<R>& ph, R* Fn) {
+  R hm = Vm[0], hp = Vp[0];
+  R unm = R(0), unp = R(0);
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    unm += Vm[1 + j] * n[j];
+    unp += Vp[1 + j] * n[j];
+  }
+  R cm = sqrt(ph.gc * fmax(hm, ph.h_floor));
+  R cp = sqrt(ph.gc * fmax(hp, ph.h_floor));
+  R SL = fmin(unm - cm, unp - cp);
+  R SR = fmax(unm + cm, unp + cp);
+  R Fm[DIM + 1], Fp[DIM + 1];
+  Fm[0] = hm * unm;
+  Fp[0] = hp * unp;
+  R pm = R(0.5) * ph.gc * hm * hm, pp = R(0.5) * ph.gc * hp * hp;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    Fm[1 + j] = hm * Vm[1 + j] * unm + pm * n[j];
+    Fp[1 + j] = hp * Vp[1 + j] * unp + pp * n[j];
+  }
+  if (SL >= R(0)) {
+#pragma unroll
+    for (int v = 0; v < DIM + 1; ++v) Fn[v] = Fm[v];
+  } else if (SR <= R(0)) {
+#pragma unroll
+    for (int v = 0; v < DIM + 1; ++v) Fn[v] = Fp[v];
+  } else {
+    R inv = R(1) / (SR - SL);
+    R Um[DIM + 1], Up[DIM + 1];
+    Um[0] = hm;
+    Up[0] = hp;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      Um[1 + j] = hm * Vm[1 + j];
+      Up[1 + j] = hp * Vp[1 + j];
+    }
+#pragma unroll
+    for (int v = 0; v < DIM + 1; ++v) Fn[v] = (SR * Fm[v] - SL * Fp[v] + SL * SR * (Up[v] - Um[v])) * inv;
+  }
+}
+
+// Q . n for one side: Q_i row 1+j = h sigma_{j i} / rho (Eq. Qterm).
+template <int DIM, typename R>
+__device__ __forceinline__ void q_normal(R h, const R* E, const R* n, const Phys<R>& ph, R* Qn) {
+  R sig[DIM][DIM];
+  stress<DIM, R>(E, ph, sig);
+  Qn[0] = R(0);
+  R hr = h * ph.rho_inv;
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    R a = R(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) a += sig[j][i] * n[i];
+    Qn[1 + j] = hr * a;
+  }
+}
+
+// ------------------------------------------------------------------ kernels
+
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(128) estep_kernel(int K, const R* __restrict__ V, R* __restrict__ E,
+                                                    const R* __restrict__ geo, const int32_t* __restrict__ nbr,
+                                                    const int8_t* __restrict__ nbrf, const R* __restrict__ fn,
+                                                    const R* __restrict__ fsj, const EstepOps<DIM, P, R> ops,
+                                                    const Phys<R> ph) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NF = S::NF, NFP = S::NFP, NE = S::NE;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  const size_t KN = (size_t)K * NP;
+  R u[DIM][NP];
+#pragma unroll
+  for (int j = 0; j < DIM; ++j)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) u[j][a] = V[(1 + j) * KN + (size_t)e * NP + a];
+  R G[2][2];
+  G[0][0] = geo[e];
+  if constexpr (DIM == 2) {
+    G[0][1] = geo[K + e];
+    G[1][0] = geo[2 * K + e];
+    G[1][1] = geo[3 * K + e];
+  }
+  const R Jinv = R(1) / geo[4 * K + e];
+  R Eo[NE][NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      R dr = R(0), ds = R(0);
+#pragma unroll
+      for (int b = 0; b < NP; ++b) {
+        dr += ops.Dr[a * NP + b] * u[j][b];
+        if constexpr (DIM == 2) ds += ops.Ds[a * NP + b] * u[j][b];
+      }
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        R v = G[0][i] * dr;
+        if constexpr (DIM == 2) v += G[1][i] * ds;
+        Eo[DIM * i + j][a] = v;
+      }
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int e2 = nbr[f * K + e];
+    R n[DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) n[i] = fn[(f * DIM + i) * K + e];
+    const R sc = fsj[f * K + e] * Jinv;
+    R gj[NFP][DIM];
+    if (e2 >= 0) {
+      const int f2 = nbrf[f * K + e];
+#pragma unroll
+      for (int k = 0; k < NFP; ++k) {
+        const int a = ops.fmask[f * NFP + k];
+        const int b = ops.fmask[f2 * NFP + (NFP - 1 - k)];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (V[(1 + j) * KN + (size_t)e2 * NP + b] - u[j][a]);
+      }
+    } else {
+      const int bc = -1 - e2;
+#pragma unroll
+      for (int k = 0; k < NFP; ++k) {
+        const int a = ops.fmask[f * NFP + k];
+        R Vm[DIM + 1], Vp[DIM + 1];
+        Vm[0] = R(1);
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) Vm[1 + j] = u[j][a];
+        ghost_V<DIM, R>(Vm, n, bc, ph, Vp);
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (Vp[1 + j] - Vm[1 + j]);
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+#pragma unroll
+      for (int k = 0; k < NFP; ++k) {
+        const R L = ops.LIFT[a * (NF * NFP) + f * NFP + k] * sc;
+#pragma unroll
+        for (int i = 0; i < DIM; ++i)
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) Eo[DIM * i + j][a] += L * n[i] * gj[k][j];
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NE; ++c)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) E[c * KN + (size_t)e * NP + a] = Eo[c][a];
+}
+
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(128) face_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E,
+                                                   const int32_t* __restrict__ fe1, const int8_t* __restrict__ ff1,
+                                                   const int32_t* __restrict__ fe2, const int8_t* __restrict__ ff2,
+                                                   const R* __restrict__ fnrm, const R* __restrict__ fsj,
+                                                   R* __restrict__ wflux, const FaceOps<DIM, P, R> ops,
+                                                   const Phys<R> ph) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV, NE = S::NE;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= F * NFQ) return;
+  const int fc = t / NFQ, m = t - fc * NFQ;
+  const size_t KN = (size_t)K * NP;
+  const int e1 = fe1[fc], f1 = ff1[fc], e2 = fe2[fc];
+  R n[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) n[i] = fnrm[(size_t)i * F + fc];
+  R Vm[NV], Vp[NV], Em[NE], Ep[NE];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) Vm[v] = R(0);
+#pragma unroll
+  for (int c = 0; c < NE; ++c) Em[c] = R(0);
+#pragma unroll
+  for (int k = 0; k < NFP; ++k) {
+    const R L = ops.Lf[m * NFP + k];
+    const size_t a = (size_t)e1 * NP + ops.fmask[f1 * NFP + k];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Vm[v] += L * V[v * KN + a];
+#pragma unroll
+    for (int c = 0; c < NE; ++c) Em[c] += L * E[c * KN + a];
+  }
+  if (e2 >= 0) {
+    const int f2 = ff2[fc];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Vp[v] = R(0);
+#pragma unroll
+    for (int c = 0; c < NE; ++c) Ep[c] = R(0);
+#pragma unroll
+    for (int k = 0; k < NFP; ++k) {
+      const R L = ops.Lf[m * NFP + k];
+      const size_t b = (size_t)e2 * NP + ops.fmask[f2 * NFP + (NFP - 1 - k)];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Vp[v] += L * V[v * KN + b];
+#pragma unroll
+      for (int c = 0; c < NE; ++c) Ep[c] += L * E[c * KN + b];
+    }
+  } else {
+    ghost_V<DIM, R>(Vm, n, -1 - e2, ph, Vp);
+    ghost_E<DIM, R>(Em, -1 - e2, ph, Ep);
+  }
+  R Fn[NV], Qm[NV], Qp[NV];
+  hll<DIM, R>(Vm, Vp, n, ph, Fn);
+  q_normal<DIM, R>(Vm[0], Em, n, ph, Qm);
+  q_normal<DIM, R>(Vp[0], Ep, n, ph, Qp);
+  const R w = ops.wf[m] * fsj[fc];
+  const size_t FQ = (size_t)F * NFQ;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) wflux[v * FQ + t] = w * (Fn[v] - R(0.5) * (Qm[v] + Qp[v]));
+}
+
+// mode 0: write dV/dt to out; mode 1: out = c0 * V0 + c1 * (Vin + dt * dV/dt).
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(128) volume_kernel(int K, int F, const R* __restrict__ Vin,
+                                                     const R* V0, R* out,
+                                                     const R* __restrict__ E, const R* __restrict__ bed,
+                                                     const R* __restrict__ geo, const int32_t* __restrict__ fid,
+                                                     const R* __restrict__ wflux, const VolOps<DIM, P, R> ops,
+                                                     const Phys<R> ph, int mode, R c0, R c1,
+                                                     const DevScalars* __restrict__ sc) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NQ = S::NQ, NF = S::NF, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV, NE = S::NE;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  const size_t KN = (size_t)K * NP;
+  const size_t eo = (size_t)e * NP;
+  R G[2][2];
+  G[0][0] = geo[e];
+  if constexpr (DIM == 2) {
+    G[0][1] = geo[K + e];
+    G[1][0] = geo[2 * K + e];
+    G[1][1] = geo[3 * K + e];
+  }
+  const R J = geo[4 * K + e];
+  R r[NV][NP];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) r[v][a] = R(0);
+
+  // ---- volume integrals: -<grad N, F - Q> - <N, S>  (Eq. WeakForm51)
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    R Vq[NV], Eq[NE];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Vq[v] = R(0);
+#pragma unroll
+    for (int c = 0; c < NE; ++c) Eq[c] = R(0);
+    R Hr = R(0), Hs = R(0);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const R l = ops.Vq[q * NP + a];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Vq[v] += l * Vin[v * KN + eo + a];
+#pragma unroll
+      for (int c = 0; c < NE; ++c) Eq[c] += l * E[c * KN + eo + a];
+      if (bed) {
+        const R H = bed[eo + a];
+        Hr += ops.Drq[q * NP + a] * H;
+        if constexpr (DIM == 2) Hs += ops.Dsq[q * NP + a] * H;
+      }
+    }
+    const R h = Vq[0];
+    R sig[DIM][DIM];
+    stress<DIM, R>(Eq, ph, sig);
+    R fx[DIM][NV];  // (Q - F) in direction i
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      fx[i][0] = -h * Vq[1 + i];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j)
+        fx[i][1 + j] = -h * Vq[1 + i] * Vq[1 + j] + h * sig[j][i] * ph.rho_inv;
+      fx[i][1 + i] -= R(0.5) * ph.gc * h * h;
+    }
+    R Sv[NV];
+    Sv[0] = R(0);
+    {
+      R dH[DIM];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        dH[i] = G[0][i] * Hr;
+        if constexpr (DIM == 2) dH[i] += G[1][i] * Hs;
+      }
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) Sv[1 + j] = -ph.gc * h * dH[j];
+      Sv[1] -= ph.gs * h;
+    }
+    R fr[NV], fs[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      fr[v] = G[0][0] * fx[0][v];
+      fs[v] = R(0);
+      if constexpr (DIM == 2) {
+        fr[v] += G[0][1] * fx[1][v];
+        fs[v] = G[1][0] * fx[0][v] + G[1][1] * fx[1][v];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const R wr = ops.Wr[q * NP + a];
+      const R ws = ops.Ws[q * NP + a];
+      const R wm = ops.wq[q] * ops.Vq[q * NP + a];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        R acc = wr * fr[v] - wm * Sv[v];
+        if constexpr (DIM == 2) acc += ws * fs[v];
+        r[v][a] += acc;
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) r[v][a] *= J;
+
+  // ---- face terms <N^-, F_bar.n - Q_bar.n> (weights and sJ folded into wflux)
+  const size_t FQ = (size_t)F * NFQ;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const uint32_t raw = (uint32_t)fid[f * K + e];
+    const bool own = (raw & 0x80000000u) == 0;
+    const size_t base = (size_t)(raw & 0x7fffffffu) * NFQ;
+    R fv[NV][NFQ];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int m = 0; m < NFQ; ++m) {
+        const R x = wflux[v * FQ + base + (own ? m : NFQ - 1 - m)];
+        fv[v][m] = own ? x : -x;
+      }
+#pragma unroll
+    for (int k = 0; k < NFP; ++k) {
+      const int a = ops.fmask[f * NFP + k];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        R acc = R(0);
+#pragma unroll
+        for (int m = 0; m < NFQ; ++m) acc += ops.LfT[k * NFQ + m] * fv[v][m];
+        r[v][a] += acc;
+      }
+    }
+  }
+
+  // ---- mass solve: M dh/dt = -r_h ; M_h du/dt = -r_u - M_u dh/dt
+  const R Jinv = R(1) / J;
+  R dV[NV][NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    R acc = R(0);
+#pragma unroll
+    for (int b = 0; b < NP; ++b) acc += ops.Minv[a * NP + b] * r[0][b];
+    dV[0][a] = -acc * Jinv;
+  }
+  R Mh[NP][NP];
+  R rhs[DIM][NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = 0; b < NP; ++b) Mh[a][b] = R(0);
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) rhs[j][a] = -r[1 + j][a] * Jinv;
+  }
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    R hq = R(0), hdq = R(0), uq[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) uq[j] = R(0);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const R l = ops.Vq[q * NP + a];
+      hq += l * Vin[eo + a];
+      hdq += l * dV[0][a];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) uq[j] += l * Vin[(1 + j) * KN + eo + a];
+    }
+    const R wh = ops.wq[q] * fmax(hq, ph.h_floor);
+    const R wd = ops.wq[q] * hdq;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const R la = ops.Vq[q * NP + a];
+      const R t = wh * la;
+#pragma unroll
+      for (int b = 0; b <= a; ++b) Mh[a][b] += t * ops.Vq[q * NP + b];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) rhs[j][a] -= wd * uq[j] * la;
+    }
+  }
+  // Cholesky of the reference-scaled M_h (lower triangle)
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = 0; b < a; ++b) {
+      R s = Mh[a][b];
+#pragma unroll
+      for (int c = 0; c < b; ++c) s -= Mh[a][c] * Mh[b][c];
+      Mh[a][b] = s / Mh[b][b];
+    }
+    R d = Mh[a][a];
+#pragma unroll
+    for (int c = 0; c < a; ++c) d -= Mh[a][c] * Mh[a][c];
+    Mh[a][a] = sqrt(d);
+  }
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    R y[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      R s = rhs[j][a];
+#pragma unroll
+      for (int c = 0; c < a; ++c) s -= Mh[a][c] * y[c];
+      y[a] = s / Mh[a][a];
+    }
+#pragma unroll
+    for (int a = NP - 1; a >= 0; --a) {
+      R s = y[a];
+#pragma unroll
+      for (int c = a + 1; c < NP; ++c) s -= Mh[c][a] * dV[1 + j][c];
+      dV[1 + j][a] = s / Mh[a][a];
+    }
+  }
+
+  // ---- output
+  if (mode == 0) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int a = 0; a < NP; ++a) out[v * KN + eo + a] = dV[v][a];
+  } else {
+    const R dt = (R)sc->dt;
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        const R vi = Vin[v * KN + eo + a];
+        R y = c1 * (vi + dt * dV[v][a]);
+        if (c0 != R(0)) y += c0 * V0[v * KN + eo + a];
+        out[v * KN + eo + a] = y;
+      }
+  }
+}
+
+// ------------------------------------------------------------------ reductions (FP64)
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Per-element stable step (see dg_swe_step), block minimum to partial[block].
+// A non-finite state sets partial to -1 (flag).
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(256) dt_partial_kernel(int K, const R* __restrict__ V, const R* __restrict__ geo,
+                                                         double gc, double h_floor, double cfl, double nu,
+                                                         double* __restrict__ partial) {
+  constexpr int NP = Sh<DIM, P>::NP;
+  __shared__ double red[8];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double dte = 1e300;
+  if (e < K) {
+    const size_t KN = (size_t)K * NP;
+    double lam = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      double h = (double)V[(size_t)e * NP + a];
+      double sp2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        double u = (double)V[(1 + j) * KN + (size_t)e * NP + a];
+        sp2 += u * u;
+      }
+      double l = sqrt(sp2) + sqrt(gc * fmax(h, h_floor));
+      if (!(l == l) || !isfinite(l) || !isfinite(h)) bad = true;
+      lam = fmax(lam, l);
+    }
+    const double dx = (double)geo[5 * K + e];
+    const double qq = 2.0 * P + 1.0;
+    dte = cfl * dx / (qq * lam + qq * qq * 2.0 * nu / dx);
+    if (bad) dte = -1.0;
+  }
+  double v = warp_min(dte);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 1e300;
+    v = warp_min(v);
+    if (lane == 0) partial[blockIdx.x] = v;
+  }
+}
+
+// Final step size: fixed dt (> 0) or min of the partials; advances t and the
+// step counter.  A negative partial latches DG_ERR_NONFINITE (4).
+__global__ void dt_finalize_kernel(int nblocks, const double* __restrict__ partial, double fixed_dt,
+                                   DevScalars* __restrict__ sc) {
+  __shared__ double red[32];
+  double v = 1e300;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) v = fmin(v, partial[i]);
+  v = warp_min(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 1e300;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmin(m, red[i]);
+    if (m < 0.0) {
+      sc->status = 4;
+      m = 0.0;
+    }
+    const double dt = fixed_dt > 0.0 ? fixed_dt : m;
+    sc->dt = dt;
+    sc->t += dt;
+    sc->steps += 1;
+    sc->dt_min = fmin(sc->dt_min, dt);
+    sc->dt_max = fmax(sc->dt_max, dt);
+  }
+}
+
+// Mass integral: sum_e J_e sum_a wint_a h_a (FP64 partial sums per block).
+template <int NP, typename R>
+__global__ void __launch_bounds__(256) mass_partial_kernel(int K, const R* __restrict__ V, const R* __restrict__ geo,
+                                                           const double* __restrict__ wint,
+                                                           double* __restrict__ partial) {
+  __shared__ double red[8];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double m = 0.0;
+  if (e < K) {
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) s += wint[a] * (double)V[(size_t)e * NP + a];
+    m = (double)geo[4 * K + e] * s;
+  }
+  double v = warp_sum(m);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 0.0;
+    v = warp_sum(v);
+    if (lane == 0) partial[blockIdx.x] = v;
+  }
+}
+
+// Compensated (Kahan) sum of the block partials; which = 0 -> mass, 1 -> mass0 too.
+__global__ void mass_finalize_kernel(int nblocks, const double* __restrict__ partial, int set_ref,
+                                     DevScalars* __restrict__ sc) {
+  if (threadIdx.x != 0) return;
+  double s = 0.0, c = 0.0;
+  for (int i = 0; i < nblocks; ++i) {
+    double y = partial[i] - c;
+    double t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  sc->mass = s;
+  if (set_ref) sc->mass0 = s;
+}
+
+template <typename Rin, typename Rout>
+__global__ void convert_kernel(size_t n, const Rin* __restrict__ in, Rout* __restrict__ out) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (Rout)in[i];
+}
+
+__global__ void reset_scalars_kernel(DevScalars* sc) {
+  sc->dt = 0.0;
+  sc->t = 0.0;
+  sc->dt_min = 1e300;
+  sc->dt_max = 0.0;
+  sc->steps = 0;
+  sc->status = 0;
+}
+
+}  // namespace dgswe
