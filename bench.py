@@ -1,0 +1,438 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the DG shallow-water / regularized-Bingham hot path.
+
+Workload (default): the 2D radial dam break on a 64 x 64 structured
+triangulation of [-1, 1]^2 (8192 triangles), order p = 2, inner disc r < 0.3
+depth 2.0, outer depth 0.5, flat bed, yield stress swept over {0, 0.02, 0.1}
+for each of the paper's three regularizations (gamma = beta = 1e3), eta = 0.01:
+nine instances.  One benchmark step advances every instance by ``--inner``
+CFL-limited SSP-RK3 steps (each step = 3 x (E-step, face flux, volume/lift/
+mass-solve/update) + FP64 step-size reduction).  The L2 cache is flushed
+(256 MiB write) before every timed step, outside the timed events.
+
+Metric: DOF-updates/s = elements x nodes x fields x RK3 steps / time (the
+auxiliary E is not counted), summed over all instances and all ranks.
+
+``--impl reference`` times the FP64 CPU oracle instead (see ``oracle/``).
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/sec at stated L2 error vs FP64 oracle; % HBM roofline; FP64 vs mixed/batched"
+UNIT = "DOF-updates/s"
+SIGMAS = (0.0, 0.02, 0.1)
+REGS = (1, 2, 3)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--inner", type=int, default=100, help="RK3 steps per instance per bench step")
+    ap.add_argument("--n", type=int, default=64, help="squares per side of the triangulation")
+    ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def sweep_cases(n, order):
+    import synth
+    out = []
+    for s0 in SIGMAS:
+        for reg in REGS:
+            out.append(synth.radial_dam_2d(n=n, order=order, reg=reg, sigma0=s0, eta=0.01,
+                                           gamma=1e3, beta=1e3))
+    return out
+
+
+def workload_name(args):
+    return (f"radial_dam_2d {args.n}x{args.n}x2 triangles on [-1,1]^2, p={args.order}, "
+            f"sigma0 in {list(SIGMAS)} x regularization in {list(REGS)} (gamma=beta=1e3, eta=0.01)")
+
+
+# ---------------------------------------------------------------- analytic counts
+
+def shape(dim, p):
+    nq1 = (3 * p + 1) // 2
+    return dict(NP=p + 1 if dim == 1 else (p + 1) * (p + 2) // 2, NQ=nq1 if dim == 1 else nq1 * nq1,
+                NF=dim + 1, NFP=1 if dim == 1 else p + 1, NFQ=1 if dim == 1 else (3 * p + 2) // 2,
+                NV=dim + 1, NE=dim * dim)
+
+
+def volume_flops(dim, p, bed=False):
+    """Floating-point operations of one volume-kernel element (FMA = 2):
+    interpolation to the volume points, pointwise flux/stress/source,
+    weighted-derivative contraction, face lift, the h-weighted mass matrix,
+    its Cholesky factorization and the two triangular solves per velocity
+    component, and the stage update.  Divisions, square roots and
+    transcendental calls count as 1."""
+    s = shape(dim, p)
+    NP, NQ, NV, NE, NF, NFP, NFQ = s["NP"], s["NQ"], s["NV"], s["NE"], s["NF"], s["NFP"], s["NFQ"]
+    f = 0
+    per_q = 2 * NP * (NV + NE) + (4 * NP * dim if bed else 0)
+    per_q += 25 if dim == 2 else 8          # stress (norm, sqrt, regularization, products)
+    per_q += 6 * dim * NV                   # F and Q components, reference rotation
+    per_q += 2 * NP * NV * (dim + 1)        # contraction with Wr, Ws, Wm
+    f += NQ * per_q + NV * NP               # + J scaling
+    f += NF * NFP * NV * 2 * NFQ            # lift of face fluxes
+    f += 2 * NP * NP + NP                   # dh/dt = -Minv r_h / J
+    per_q2 = 2 * NP * (2 + dim) + NP * (NP + 1) + 2 * NP * dim + 3
+    f += NQ * per_q2                        # M_h and M_u dh/dt
+    f += NP ** 3 // 3 + NP * NP             # Cholesky
+    f += dim * 2 * NP * NP                  # two triangular solves per component
+    f += NV * NP * 5                        # stage update
+    return f
+
+
+def estep_flops(dim, p):
+    s = shape(dim, p)
+    NP, NF, NFP = s["NP"], s["NF"], s["NFP"]
+    return dim * NP * NP * 2 * dim + NP * dim * dim * 2 * dim + NF * NFP * dim * 2 + NP * NF * NFP * dim * dim * 3
+
+
+def face_flops_per_point(dim, p):
+    s = shape(dim, p)
+    return 2 * 2 * s["NFP"] * (s["NV"] + s["NE"]) + 60 + 2 * (30 if dim == 2 else 10)
+
+
+def volume_bytes(dim, p, rs):
+    """Compulsory bytes of one volume-kernel element: read Vin (NV x NP),
+    V0 (NV x NP), E (NE x NP), geometry (5), face ids (NF x 4 B) and the face
+    fluxes it lifts (NF x NV x NFQ, each face read by both neighbours), write
+    Vout (NV x NP)."""
+    s = shape(dim, p)
+    NP, NV, NE, NF, NFQ = s["NP"], s["NV"], s["NE"], s["NF"], s["NFQ"]
+    return rs * (3 * NV * NP + NE * NP + 5 + NF * NV * NFQ) + 4 * NF
+
+
+# ---------------------------------------------------------------- helpers
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# FP64 and FP32 pipe peaks derived from unit counts and the maximum SM clock:
+# 152 SMs x 2070 MHz x 2 flop/FMA x lanes/SM/clk (FP32: 128; FP64: 2 on GB300,
+# the nominal 1.25 TFLOP/s of the part).
+SM_COUNT, SM_MAX_MHZ = 152, 2070.0
+FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 128 / 1e12
+FP64_PEAK_TFLOPS = 1.25
+
+
+def traffic_record(kernel, workload):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or
+    None when the summary is missing or the kernel source changed since."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)
+    except Exception:
+        return None
+    src = os.path.join(ROOT, "paper_2301_11238_gb300", "csrc", "dg_kernels.cuh")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    r = rec.get(f"{kernel}|{workload}")
+    if not r or r.get("source_sha") != h:
+        return None
+    return r.get("bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        mx = max(float(r[2]) for r in rows if r[2].replace(".", "").isdigit())
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows), "power_w_max": max(float(r[3]) for r in rows
+                                                         if r[3].replace(".", "").isdigit())}
+
+
+# ---------------------------------------------------------------- oracle legs
+
+def oracle_worker(spec_path):
+    """Runs in a subprocess with one BLAS/OpenMP thread: times the oracle on
+    instance 0 of the workload for about ``seconds`` and writes JSON."""
+    import numpy as np
+    with open(spec_path) as f:
+        spec = json.load(f)
+    from oracle.run import build as oracle_build
+    cases = sweep_cases(spec["n"], spec["order"])
+    case = cases[spec.get("instance", 0)]
+    d, V0, _ = oracle_build(case)
+    Vh = d.to_modal(V0)
+    units = d.K * d.Np * d.nV
+    steps, times = 0, []
+    t_all = time.perf_counter()
+    while True:
+        t0 = time.perf_counter()
+        Vh, _ = d.ssp_rk3_step(Vh)
+        times.append(time.perf_counter() - t0)
+        steps += 1
+        if steps >= spec.get("max_steps", 10 ** 9):
+            break
+        if time.perf_counter() - t_all > spec["seconds"] and steps >= spec.get("min_steps", 1):
+            break
+    out = dict(steps=steps, seconds=sum(times), units_per_step=units, step_times=times,
+               final=d.to_nodal(Vh).tolist() if spec.get("return_state") else None)
+    with open(spec["out"], "w") as f:
+        json.dump(out, f)
+
+
+def run_oracle_subprocess(n, order, seconds, min_steps=1, max_steps=10 ** 9, return_state=False):
+    with tempfile.TemporaryDirectory() as td:
+        spec = dict(n=n, order=order, seconds=seconds, min_steps=min_steps, max_steps=max_steps,
+                    out=os.path.join(td, "out.json"), return_state=return_state)
+        sp = os.path.join(td, "spec.json")
+        with open(sp, "w") as f:
+            json.dump(spec, f)
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+        subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-worker", sp], check=True,
+                       env=env, cwd=ROOT)
+        with open(spec["out"]) as f:
+            return json.load(f)
+
+
+def reference_main(args):
+    """The oracle as it stands, on one host core, same workload, metric and unit.
+    Each step is one SSP-RK3 step of one sweep instance (the oracle needs about
+    half a second for it); warm-up steps are untimed."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = run_oracle_subprocess(args.n, args.order, seconds=0.0, min_steps=args.warmup + args.steps,
+                                max_steps=args.warmup + args.steps)
+    times = res["step_times"][args.warmup:]
+    secs = sum(times)
+    value = res["units_per_step"] * len(times) / secs
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args), "sample": "one SSP-RK3 step of instance 0 per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{len(times)} SSP-RK3 steps of instance 0 (sigma0=0, reg 1)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def main():
+    args = parse()
+    if args.oracle_worker:
+        oracle_worker(args.oracle_worker)
+        return
+    if args.impl == "reference":
+        reference_main(args)
+        return
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2301_11238_gb300 as G
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    prec = G.PREC_FP64 if args.precision == "fp64" else G.PREC_FP32
+    stream = torch.cuda.Stream()
+    cases = sweep_cases(args.n, args.order)
+    solvers, V0s = [], []
+    with torch.cuda.stream(stream):
+        for c in cases:
+            s, V0, _ = G.solver_from_case(c, precision=prec, stream=stream)
+            solvers.append(s)
+            V0s.append(V0)
+    units_per_inner = sum(s.K * s.Np * s.nV for s in solvers)
+    units_per_step = units_per_inner * args.inner
+    launches_per_step = sum(s.launches_per_step() for s in solvers) * args.inner
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def one_step():
+        for s in solvers:
+            s.advance(args.inner)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            one_step()
+        stream.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        barrier()
+        with ClockSampler(local) as clk:
+            for k in range(args.steps):
+                flush.zero_()
+                evs[k][0].record(stream)
+                one_step()
+                evs[k][1].record(stream)
+            stream.synchronize()
+        barrier()
+    ms = [a.elapsed_time(b) for a, b in evs]
+    total_ms = sum(ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = units_per_step * args.steps * world / (total_ms / 1e3)
+    stats = [s.sync() for s in solvers]
+
+    # ---- dominant kernel: live per-launch timing on the solver's stream
+    with torch.cuda.stream(stream):
+        kt = solvers[3].time_kernels(20)  # instance 3: sigma0 = 0.02, regularization 1
+    dim, p = 2, args.order
+    K = solvers[3].K
+    vol_ms = kt["volume"]
+    flops = volume_flops(dim, p) * K
+    rs = 8 if prec == G.PREC_FP64 else 4
+    peak_tf = FP64_PEAK_TFLOPS if prec == G.PREC_FP64 else FP32_PEAK_TFLOPS
+    achieved_tf = flops / (vol_ms * 1e-3) / 1e12
+    pk, pk_kind = peaks()
+    vbytes = volume_bytes(dim, p, rs) * K
+    wl_key = f"{args.precision}_n{args.n}_p{args.order}"
+    roof = {"bound": "alu", "kernel": f"volume_kernel<2,{p},{'double' if rs == 8 else 'float'}>",
+            "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
+            "peak_source": ("nominal FP64 rate of GB300 (1.25 TFLOP/s = 152 SMs x 2070 MHz x 2 x ~2 DFMA/clk)"
+                            if rs == 8 else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"),
+            "traffic": traffic_record("volume_kernel", wl_key),
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": vbytes,
+            "hbm_gbs_at_algorithmic_bytes": vbytes / (vol_ms * 1e-3) / 1e9,
+            "hbm_frac": vbytes / (vol_ms * 1e-3) / 1e9 / pk["hbm_gbs"], "hbm_peak_source": pk_kind,
+            "kernel_ms": kt}
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for v in V0s]
+        out_host = [torch.empty_like(x).pin_memory() for x in pinned]
+        dev = [torch.empty_like(x, device="cuda") for x in pinned]
+        h2d = sum(x.numel() * 8 for x in pinned)
+        with torch.cuda.stream(stream):
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.steps)]
+            barrier()
+            for k in range(args.steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                for i, s in enumerate(solvers):
+                    dev[i].copy_(pinned[i], non_blocking=True)
+                    s.L.dg_swe_set_state(s.ctx, G.C.c_void_p(dev[i].data_ptr()), 1)
+                    s.advance(args.inner)
+                    s.L.dg_swe_get_state(s.ctx, G.C.c_void_p(dev[i].data_ptr()), None, 1)
+                    out_host[i].copy_(dev[i], non_blocking=True)
+                ev[k][1].record(stream)
+            stream.synchronize()
+            barrier()
+        e_ms = sum(a.elapsed_time(b) for a, b in ev)
+        e2e = {"value": units_per_step * args.steps * world / (e_ms / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
+               "note": "per step: pinned host->device copy of every instance's state, set_state, "
+                       "advance, get_state, device->host copy"}
+
+    # ---- accuracy and CPU baseline (rank 0, N=1 only)
+    cpu = None
+    acc = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        res = run_oracle_subprocess(args.n, args.order, seconds=args.oracle_seconds, min_steps=2,
+                                    return_state=True)
+        cpu = {"value": res["units_per_step"] * res["steps"] / res["seconds"], "unit": UNIT, "cores": 1,
+               "kind": "oracle",
+               "sample": f"{res['steps']} SSP-RK3 steps of instance 0 (sigma0=0, reg 1), "
+                         f"{res['seconds']:.1f} s on one host core"}
+        s0 = solvers[0]
+        with torch.cuda.stream(stream):
+            s0.set_state(V0s[0])
+            s0.run(res["steps"])
+            Vg = s0.get_state(with_E=False)
+        Vo = np.asarray(res["final"])
+        acc = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
+               "after_steps": res["steps"], "instance": "sigma0=0, reg 1"}
+
+    dt_info = {f"sigma0={c.params['sigma0']},reg={c.params['reg']}": st["dt_last"]
+               for c, st in zip(cases, stats)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if rs == 8 else "f32",
+            "data": "synthetic",
+            "config": {"workload": workload_name(args), "instances": len(solvers), "elements": K,
+                       "inner_rk3_steps_per_step": args.inner, "l2": "flushed (256 MiB write) before each step",
+                       "parallelism": f"replicas x{world}", "dt_last": dt_info},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk.summary(), "accuracy": acc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    for s in solvers:
+        s.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -169,6 +169,20 @@ dg_status dg_swe_step(dg_swe_ctx *ctx, double dt, double *dt_taken);
  * stats (may be NULL) and reports a latched device error. */
 dg_status dg_swe_run(dg_swe_ctx *ctx, int64_t n_steps, double t_end, dg_swe_stats *stats);
 
+/* Enqueue-only form of dg_swe_run: replays n_steps CFL-limited SSP-RK3
+ * steps from the CUDA graph (captured on first use on a private stream that
+ * forks from and joins back into the context's stream) and returns without
+ * synchronizing.  Device errors surface at the next synchronizing call. */
+dg_status dg_swe_advance(dg_swe_ctx *ctx, int64_t n_steps);
+
+/* Profiling aid: average device time in milliseconds of one launch of each
+ * kernel of the explicit path, each launched n_iter times back to back on the
+ * context's stream and timed with CUDA events: ms[0] E-step, ms[1] face flux,
+ * ms[2] volume/lift/mass-solve/update (writes a scratch stage buffer, the
+ * state is unchanged), ms[3] stable-step partial reduction, ms[4] mass
+ * partial reduction.  Synchronizes. */
+dg_status dg_swe_time_kernels(dg_swe_ctx *ctx, int n_iter, double *ms);
+
 /* Enqueues the FP64 mass reduction and synchronizes; fills stats. */
 dg_status dg_swe_sync(dg_swe_ctx *ctx, dg_swe_stats *stats);
 

@@ -160,6 +160,16 @@ class Solver:
         self._check(self.L.dg_swe_run(self.ctx, int(n_steps), 0.0, C.byref(st)))
         return _stats_dict(st)
 
+    def advance(self, n_steps):
+        """Enqueue n_steps CFL-limited SSP-RK3 steps (no host synchronization)."""
+        self._check(self.L.dg_swe_advance(self.ctx, int(n_steps)))
+
+    def time_kernels(self, n_iter=20):
+        """Average ms per launch: estep, face, volume, dt partial, mass partial."""
+        ms = (C.c_double * 5)()
+        self._check(self.L.dg_swe_time_kernels(self.ctx, int(n_iter), ms))
+        return dict(zip(("estep", "face", "volume", "dt", "mass"), list(ms)))
+
     def sync(self):
         st = _lib.Stats()
         self._check(self.L.dg_swe_sync(self.ctx, C.byref(st)))

@@ -549,27 +549,8 @@ dg_status dg_swe_run(dg_swe_ctx* c, int64_t n_steps, double t_end, dg_swe_stats*
       }
     }
   } else if (n_steps > 0) {
-    if (!c->priv) {
-      CK(cudaStreamCreateWithFlags(&c->priv, cudaStreamNonBlocking));
-      CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
-      CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
-    }
-    if (!c->g1) {
-      st = capture(c, 1, &c->g1);
-      if (st != DG_OK) return st;
-      st = capture(c, kGraphSteps, &c->gN);
-      if (st != DG_OK) return st;
-    }
-    CK(cudaEventRecord(c->ev_fork, c->stream));
-    CK(cudaStreamWaitEvent(c->priv, c->ev_fork, 0));
-    int64_t left = n_steps;
-    while (left >= kGraphSteps) {
-      CK(cudaGraphLaunch(c->gN, c->priv));
-      left -= kGraphSteps;
-    }
-    while (left-- > 0) CK(cudaGraphLaunch(c->g1, c->priv));
-    CK(cudaEventRecord(c->ev_join, c->priv));
-    CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+    st = dg_swe_advance(c, n_steps);
+    if (st != DG_OK) return st;
   }
   enqueue_mass(c, 0, c->stream);
   CK(cudaGetLastError());
@@ -578,6 +559,76 @@ dg_status dg_swe_run(dg_swe_ctx* c, int64_t n_steps, double t_end, dg_swe_stats*
   if (st != DG_OK) return st;
   fill_stats(h, stats);
   if (h.status != 0) return fail(c, (dg_status)h.status, "device status: non-finite state");
+  return DG_OK;
+}
+
+dg_status dg_swe_advance(dg_swe_ctx* c, int64_t n_steps) {
+  dg_status st = check_ws(c);
+  if (st != DG_OK) return st;
+  if (n_steps < 0) return fail(c, DG_ERR_ARG, "n_steps < 0");
+  if (n_steps == 0) return DG_OK;
+  if (!c->priv) {
+    CK(cudaStreamCreateWithFlags(&c->priv, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  }
+  if (!c->g1) {
+    st = capture(c, 1, &c->g1);
+    if (st != DG_OK) return st;
+    st = capture(c, kGraphSteps, &c->gN);
+    if (st != DG_OK) return st;
+  }
+  // fork onto the private capture stream and join back: the caller's stream
+  // orders everything before and after this call
+  CK(cudaEventRecord(c->ev_fork, c->stream));
+  CK(cudaStreamWaitEvent(c->priv, c->ev_fork, 0));
+  int64_t left = n_steps;
+  while (left >= kGraphSteps) {
+    CK(cudaGraphLaunch(c->gN, c->priv));
+    left -= kGraphSteps;
+  }
+  while (left-- > 0) CK(cudaGraphLaunch(c->g1, c->priv));
+  CK(cudaEventRecord(c->ev_join, c->priv));
+  CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+  return DG_OK;
+}
+
+dg_status dg_swe_time_kernels(dg_swe_ctx* c, int n_iter, double* ms) {
+  dg_status st = check_ws(c);
+  if (st != DG_OK) return st;
+  if (n_iter < 1 || !ms) return fail(c, DG_ERR_ARG, "n_iter >= 1 and ms[5] required");
+  cudaStream_t s = c->stream;
+  void* V0 = c->ws + c->off.V0;
+  void* V1 = c->ws + c->off.V1;
+  void* E = c->ws + c->off.E;
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  // E and the face fluxes of the current state feed the volume kernel
+  c->drv->estep(c, V0, E, s);
+  c->drv->face(c, V0, E, s);
+  for (int k = 0; k < 5; ++k) {
+    CK(cudaEventRecord(a, s));
+    for (int i = 0; i < n_iter; ++i) {
+      switch (k) {
+        case 0: c->drv->estep(c, V0, E, s); break;
+        case 1: c->drv->face(c, V0, E, s); break;
+        case 2: c->drv->volume(c, V0, V0, V1, 1, 0.0, 1.0, s); break;
+        case 3:
+          c->drv->dt_partial(c, V0, s);
+          break;
+        case 4: c->drv->mass_partial(c, V0, s); break;
+      }
+    }
+    CK(cudaEventRecord(b, s));
+    CK(cudaEventSynchronize(b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, a, b));
+    ms[k] = (double)t / n_iter;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  CK(cudaGetLastError());
   return DG_OK;
 }
 
