@@ -186,6 +186,37 @@ dg_status dg_swe_time_kernels(dg_swe_ctx *ctx, int n_iter, double *ms);
 /* Enqueues the FP64 mass reduction and synchronizes; fills stats. */
 dg_status dg_swe_sync(dg_swe_ctx *ctx, dg_swe_stats *stats);
 
+/* Size of the library's static device scratch array used by
+ * dg_swe_residual_static: 16 MiB, held on every GPU that loads the library
+ * until the process exits. */
+#define DG_SWE_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* Allocation-free variant of dg_swe_residual (the paper has no counterpart;
+ * this is a deployment convenience).  It is meant for callers that must not
+ * allocate device memory per call: a host application that reserved its whole
+ * device-memory budget at start-up, or code on a latency-critical path where
+ * cudaMalloc (which may synchronize the device) is off limits.  Same inputs,
+ * outputs and result as dg_swe_residual, but the per-call scratch (E and the
+ * face fluxes, plus FP32 staging buffers for DG_PREC_FP32 contexts) lives in a
+ * file-scope __device__ array of DG_SWE_STATIC_SCRATCH_BYTES instead of the
+ * workspace scratch region; the context's geometry and operators are still
+ * read from its workspace.  The call allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library routine).
+ *  - Problems whose scratch need (dg_swe_static_scratch_need) exceeds the
+ *    array are rejected with DG_ERR_ARG and a message giving both sizes.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) for that device; make that first call before any
+ *    CUDA stream capture.
+ *  - All calls in the process share the one array, which keeps the contents
+ *    of the last call; every word is written before it is read, so no
+ *    clearing is needed.  Calls whose work overlaps on the GPU (different
+ *    streams or contexts without ordering between them) race on the array
+ *    and must be serialized by the caller. */
+dg_status dg_swe_residual_static(dg_swe_ctx *ctx, const double *V_dev, double *dVdt_dev, double *E_dev);
+
+/* Scratch bytes dg_swe_residual_static needs for this context. */
+size_t dg_swe_static_scratch_need(const dg_swe_ctx *ctx);
+
 /* Number of kernel launches one dg_swe_step enqueues (for launch accounting). */
 int32_t dg_swe_launches_per_step(const dg_swe_ctx *ctx);
 

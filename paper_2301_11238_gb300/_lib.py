@@ -61,6 +61,8 @@ _SIGS = {
     "dg_swe_advance": (C.c_int, [C.c_void_p, C.c_int64]),
     "dg_swe_time_kernels": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double)]),
     "dg_swe_launches_per_step": (C.c_int32, [C.c_void_p]),
+    "dg_swe_residual_static": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_swe_static_scratch_need": (C.c_size_t, [C.c_void_p]),
     "dg_swe_last_error": (C.c_char_p, [C.c_void_p]),
     "dg_swe_destroy": (None, [C.c_void_p]),
 }

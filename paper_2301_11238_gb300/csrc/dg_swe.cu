@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -75,6 +76,11 @@ struct Driver {
                       double c1, cudaStream_t s) = 0;
   virtual void dt_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
   virtual void mass_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
+  // Face flux and residual-mode volume pass with caller-chosen scratch for
+  // the face fluxes and E (used by dg_swe_residual_static).
+  virtual void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) = 0;
+  virtual void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
+                             cudaStream_t s) = 0;
 };
 
 template <typename R>
@@ -161,6 +167,22 @@ struct Impl final : Driver {
         K, F, (const R*)Vin, (const R*)V0, (R*)out, c->at<R>(c->off.E),
         c->has_bed ? c->at<R>(c->off.bed) : nullptr, c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid),
         c->at<R>(c->off.wflux), vo, ph, mode, (R)c0, (R)c1, c->at<DevScalars>(c->off.sc));
+  }
+  void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) override {
+    const int K = (int)c->mesh.K, F = (int)c->mesh.F;
+    const long long n = (long long)F * S::NFQ;
+    face_kernel<DIM, P, R><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+        K, F, (const R*)V, (const R*)E, c->at<int32_t>(c->off.fe1), c->at<int8_t>(c->off.ff1),
+        c->at<int32_t>(c->off.fe2), c->at<int8_t>(c->off.ff2), c->at<R>(c->off.fnrm), c->at<R>(c->off.fsjf),
+        (R*)wflux, fo, ph);
+  }
+  void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
+                     cudaStream_t s) override {
+    const int K = (int)c->mesh.K, F = (int)c->mesh.F;
+    volume_kernel<DIM, P, R><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+        K, F, (const R*)V, nullptr, (R*)out, (const R*)E, c->has_bed ? c->at<R>(c->off.bed) : nullptr,
+        c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid), (const R*)wflux, vo, ph, 0, R(0), R(0),
+        c->at<DevScalars>(c->off.sc));
   }
   void dt_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) override {
     const int K = (int)c->mesh.K;
@@ -646,6 +668,89 @@ dg_status dg_swe_sync(dg_swe_ctx* c, dg_swe_stats* stats) {
 }
 
 int32_t dg_swe_launches_per_step(const dg_swe_ctx* c) { return c ? 11 : 0; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Scratch for dg_swe_residual_static: a file-scope device array, so that the
+// call needs no device allocation of its own.  Every GPU that loads the
+// library holds these bytes until the process exits.  Host code only ever
+// sees a stand-in symbol here; its device address comes from
+// cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_static_scratch[DG_SWE_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device (looked up on the
+// first call per device).
+dg_status static_scratch(dg_swe_ctx* c, void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(c, DG_ERR_UNSUPPORTED, "device ordinal beyond 63");
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(c, e, "cudaGetSymbolAddress(g_static_scratch)");
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return DG_OK;
+}
+}  // namespace
+
+extern "C" {
+
+size_t dg_swe_static_scratch_need(const dg_swe_ctx* c) {
+  if (!c) return 0;
+  const size_t np = (size_t)c->mesh.K * c->ops.Np;
+  size_t need = align256((size_t)c->dim * c->dim * np * c->rsize)                        // E
+              + align256((size_t)(c->dim + 1) * c->mesh.F * c->ops.Nfq * c->rsize);     // face fluxes
+  if (c->rsize == 4) need += 2 * align256((size_t)(c->dim + 1) * np * 4);                // FP32 in/out
+  return need;
+}
+
+dg_status dg_swe_residual_static(dg_swe_ctx* c, const double* V_dev, double* dVdt_dev, double* E_dev) {
+  dg_status st = check_ws(c);
+  if (st != DG_OK) return st;
+  if (!V_dev || !dVdt_dev) return fail(c, DG_ERR_ARG, "null device pointer");
+  const size_t need = dg_swe_static_scratch_need(c);
+  if (need > (size_t)DG_SWE_STATIC_SCRATCH_BYTES)
+    return fail(c, DG_ERR_ARG, "problem needs " + std::to_string(need) + " scratch bytes; the static scratch holds " +
+                                   std::to_string((size_t)DG_SWE_STATIC_SCRATCH_BYTES));
+  char* base = nullptr;
+  st = static_scratch(c, (void**)&base);
+  if (st != DG_OK) return st;
+  const size_t np = (size_t)c->mesh.K * c->ops.Np;
+  const size_t nv = (size_t)(c->dim + 1) * np, ne = (size_t)c->dim * c->dim * np;
+  char* E = base;
+  char* wflux = E + align256(ne * c->rsize);
+  char* tail = wflux + align256((size_t)(c->dim + 1) * c->mesh.F * c->ops.Nfq * c->rsize);
+  cudaStream_t s = c->stream;
+  // Every scratch word is written (E by the E-step, fluxes by the face pass)
+  // before it is read, so nothing left by an earlier call needs clearing.
+  if (c->rsize == 8) {
+    c->drv->estep(c, V_dev, E, s);
+    c->drv->face_into(c, V_dev, E, wflux, s);
+    c->drv->residual_from(c, V_dev, E, wflux, dVdt_dev, s);
+    if (E_dev) CK(cudaMemcpyAsync(E_dev, E, ne * 8, cudaMemcpyDeviceToDevice, s));
+  } else {
+    char* Vf = tail;
+    char* Of = tail + align256(nv * 4);
+    convert<double, float>(V_dev, Vf, nv, s);
+    c->drv->estep(c, Vf, E, s);
+    c->drv->face_into(c, Vf, E, wflux, s);
+    c->drv->residual_from(c, Vf, E, wflux, Of, s);
+    convert<float, double>(Of, dVdt_dev, nv, s);
+    if (E_dev) convert<float, double>(E, E_dev, ne, s);
+  }
+  CK(cudaGetLastError());
+  return DG_OK;
+}
 
 const char* dg_swe_last_error(const dg_swe_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
