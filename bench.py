@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--mode", default="batch", choices=["batch", "solo"],
+                    help="batch: all instances in one dg_batch (one launch per phase); solo: one context each")
     ap.add_argument("--inner", type=int, default=100, help="RK3 steps per instance per bench step")
     ap.add_argument("--n", type=int, default=64, help="squares per side of the triangulation")
     ap.add_argument("--order", type=int, default=2)
@@ -300,15 +302,21 @@ def main():
     prec = G.PREC_FP64 if args.precision == "fp64" else G.PREC_FP32
     stream = torch.cuda.Stream()
     cases = sweep_cases(args.n, args.order)
-    solvers, V0s = [], []
+    batch, solvers, V0s, tiles = None, [], [], None
     with torch.cuda.stream(stream):
-        for c in cases:
-            s, V0, _ = G.solver_from_case(c, precision=prec, stream=stream)
-            solvers.append(s)
-            V0s.append(V0)
-    units_per_inner = sum(s.K * s.Np * s.nV for s in solvers)
+        if args.mode == "batch":
+            batch, V0s = G.batch_from_cases(cases, precision=prec, stream=stream)
+            tiles = batch.autotune(5)
+            units_per_inner = batch.info()["dofs"]
+            launches_per_step = batch.launches_per_step() * args.inner
+        else:
+            for c in cases:
+                s, V0, _ = G.solver_from_case(c, precision=prec, stream=stream)
+                solvers.append(s)
+                V0s.append(V0)
+            units_per_inner = sum(s.K * s.Np * s.nV for s in solvers)
+            launches_per_step = sum(s.launches_per_step() for s in solvers) * args.inner
     units_per_step = units_per_inner * args.inner
-    launches_per_step = sum(s.launches_per_step() for s in solvers) * args.inner
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
@@ -317,8 +325,11 @@ def main():
         torch.cuda.synchronize()
 
     def one_step():
-        for s in solvers:
-            s.advance(args.inner)
+        if batch is not None:
+            batch.advance(args.inner)
+        else:
+            for s in solvers:
+                s.advance(args.inner)
 
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -342,13 +353,17 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
     value = units_per_step * args.steps * world / (total_ms / 1e3)
-    stats = [s.sync() for s in solvers]
+    stats = batch.stats() if batch is not None else [s.sync() for s in solvers]
 
-    # ---- dominant kernel: live per-launch timing on the solver's stream
+    # ---- dominant kernel: live per-launch timing on the launching stream
     with torch.cuda.stream(stream):
-        kt = solvers[3].time_kernels(20)  # instance 3: sigma0 = 0.02, regularization 1
+        if batch is not None:
+            kt = batch.time_kernels(20)[0]
+            K = batch.info()["elements"]
+        else:
+            kt = solvers[3].time_kernels(20)  # instance 3: sigma0 = 0.02, regularization 1
+            K = solvers[3].K
     dim, p = 2, args.order
-    K = solvers[3].K
     vol_ms = kt["volume"]
     flops = volume_flops(dim, p) * K
     rs = 8 if prec == G.PREC_FP64 else 4
@@ -356,12 +371,15 @@ def main():
     achieved_tf = flops / (vol_ms * 1e-3) / 1e12
     pk, pk_kind = peaks()
     vbytes = volume_bytes(dim, p, rs) * K
-    wl_key = f"{args.precision}_n{args.n}_p{args.order}"
-    roof = {"bound": "alu", "kernel": f"volume_kernel<2,{p},{'double' if rs == 8 else 'float'}>",
+    wl_key = f"{args.mode}_{args.precision}_n{args.n}_p{args.order}"
+    roof = {"bound": "alu", "kernel": f"volume_kernel<2,{p},{'double' if rs == 8 else 'float'},"
+                                      f"{'true' if batch is not None else 'false'}>",
             "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-            "peak_source": ("nominal FP64 rate of GB300 (1.25 TFLOP/s = 152 SMs x 2070 MHz x 2 x ~2 DFMA/clk)"
-                            if rs == 8 else "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"),
+            "peak_source": ("FP64 pipe: 152 SMs x 2070 MHz x 2 flop x 2 DFMA/clk/SM = 1.26 TFLOP/s "
+                            "(nominal 1.25; 1.255 measured by an FMA probe)"
+                            if rs == 8 else "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz"),
             "traffic": traffic_record("volume_kernel", wl_key),
+            "elements_per_launch": K,
             "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": vbytes,
             "hbm_gbs_at_algorithmic_bytes": vbytes / (vol_ms * 1e-3) / 1e9,
             "hbm_frac": vbytes / (vol_ms * 1e-3) / 1e9 / pk["hbm_gbs"], "hbm_peak_source": pk_kind,
@@ -381,11 +399,22 @@ def main():
             for k in range(args.steps):
                 flush.zero_()
                 ev[k][0].record(stream)
-                for i, s in enumerate(solvers):
+                for i in range(len(V0s)):
                     dev[i].copy_(pinned[i], non_blocking=True)
-                    s.L.dg_swe_set_state(s.ctx, G.C.c_void_p(dev[i].data_ptr()), 1)
-                    s.advance(args.inner)
-                    s.L.dg_swe_get_state(s.ctx, G.C.c_void_p(dev[i].data_ptr()), None, 1)
+                    if batch is not None:
+                        batch.set_state(i, dev[i])
+                    else:
+                        solvers[i].set_state(dev[i])
+                if batch is not None:
+                    batch.advance(args.inner)
+                else:
+                    for s in solvers:
+                        s.advance(args.inner)
+                for i in range(len(V0s)):
+                    if batch is not None:
+                        batch.get_state_device(i, dev[i])
+                    else:
+                        solvers[i].get_state_device(dev[i])
                     out_host[i].copy_(dev[i], non_blocking=True)
                 ev[k][1].record(stream)
             stream.synchronize()
@@ -406,11 +435,15 @@ def main():
                "kind": "oracle",
                "sample": f"{res['steps']} SSP-RK3 steps of instance 0 (sigma0=0, reg 1), "
                          f"{res['seconds']:.1f} s on one host core"}
-        s0 = solvers[0]
         with torch.cuda.stream(stream):
-            s0.set_state(V0s[0])
-            s0.run(res["steps"])
-            Vg = s0.get_state(with_E=False)
+            if batch is not None:
+                batch.set_state(0, V0s[0])
+                batch.run(res["steps"])
+                Vg = batch.get_state(0)
+            else:
+                solvers[0].set_state(V0s[0])
+                solvers[0].run(res["steps"])
+                Vg = solvers[0].get_state(with_E=False)
         Vo = np.asarray(res["final"])
         acc = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
                "after_steps": res["steps"], "instance": "sigma0=0, reg 1"}
@@ -421,7 +454,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if rs == 8 else "f32",
             "data": "synthetic",
-            "config": {"workload": workload_name(args), "instances": len(solvers), "elements": K,
+            "config": {"workload": workload_name(args), "instances": len(V0s), "elements_total": K
+                       if batch is not None else K * len(V0s), "mode": args.mode, "tiles": tiles,
                        "inner_rk3_steps_per_step": args.inner, "l2": "flushed (256 MiB write) before each step",
                        "parallelism": f"replicas x{world}", "dt_last": dt_info},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
@@ -430,6 +464,8 @@ def main():
         print(json.dumps(line), flush=True)
     for s in solvers:
         s.close()
+    if batch is not None:
+        batch.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -208,3 +208,160 @@ def solver_from_case(case, precision=PREC_FP64, order=None, with_state=True, str
     if with_state:
         s.set_state(V0)
     return s, V0, bed
+
+
+class Batch:
+    """Many independent instances advanced together (include/dg_batch.h).
+
+    ``specs`` is a list of dicts with keys dim, coords, etov, order, reg, prm
+    and optionally face_bc, bcs, bed.  All instances share ``precision``."""
+
+    def __init__(self, specs, precision=PREC_FP64, device="cuda", stream=None, allocate=True):
+        self.L = _lib.lib()
+        n = len(specs)
+        self.n = n
+        self._keep = []
+        meshes = (_lib.Mesh * n)()
+        params = (_lib.Params * n)()
+        orders = (C.c_int * n)()
+        regs = (C.c_int * n)()
+        self.shapes = []
+        for i, sp in enumerate(specs):
+            dim = int(sp["dim"])
+            coords = np.ascontiguousarray(sp["coords"], dtype=np.float64).reshape(-1, dim)
+            etov = np.ascontiguousarray(sp["etov"], dtype=np.int32)
+            fb = sp.get("face_bc")
+            fb = None if fb is None else np.ascontiguousarray(fb, dtype=np.int8)
+            bed = sp.get("bed")
+            bed = None if bed is None else np.ascontiguousarray(bed, dtype=np.float64)
+            self._keep += [coords, etov, fb, bed]
+            m = meshes[i]
+            m.dim = dim
+            m.n_vertices = coords.shape[0]
+            m.coords = coords.ctypes.data
+            m.n_elements = etov.shape[0]
+            m.elem_vertices = etov.ctypes.data
+            m.face_bc = None if fb is None else fb.ctypes.data
+            m.bed = None if bed is None else bed.ctypes.data
+            params[i] = make_params(sp["prm"], sp.get("bcs"), precision)
+            orders[i] = int(sp["order"])
+            regs[i] = int(sp["reg"])
+            p = int(sp["order"])
+            np_ = p + 1 if dim == 1 else (p + 1) * (p + 2) // 2
+            self.shapes.append((dim + 1, etov.shape[0], np_))
+        ctx = C.c_void_p()
+        st = self.L.dg_batch_init(n, meshes, orders, regs, params, C.byref(ctx))
+        self.ctx = ctx
+        if st != DG_OK:
+            msg = self.L.dg_batch_last_error(ctx).decode() if ctx.value else ""
+            if ctx.value:
+                self.L.dg_batch_destroy(ctx)
+                self.ctx = C.c_void_p()
+            raise DGError(st, msg)
+        self.workspace = None
+        if allocate:
+            self.allocate(device, stream)
+
+    def allocate(self, device="cuda", stream=None):
+        torch = _torch()
+        nbytes = int(self.L.dg_batch_workspace_size(self.ctx))
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
+        self._check(self.L.dg_batch_set_stream(self.ctx, C.c_void_p(self.stream.cuda_stream)))
+        self._check(self.L.dg_batch_set_workspace(self.ctx, C.c_void_p(self.workspace.data_ptr()), nbytes))
+
+    def _check(self, st):
+        if st != DG_OK:
+            raise DGError(st, self.L.dg_batch_last_error(self.ctx).decode())
+
+    def set_state(self, i, V):
+        if isinstance(V, np.ndarray):
+            V = np.ascontiguousarray(V, dtype=np.float64)
+            assert V.shape == self.shapes[i]
+            self._check(self.L.dg_batch_set_state(self.ctx, int(i), V.ctypes.data, 0))
+        else:
+            assert tuple(V.shape) == self.shapes[i] and V.is_cuda and V.is_contiguous()
+            self._check(self.L.dg_batch_set_state(self.ctx, int(i), C.c_void_p(V.data_ptr()), 1))
+
+    def get_state(self, i):
+        V = np.empty(self.shapes[i])
+        self._check(self.L.dg_batch_get_state(self.ctx, int(i), V.ctypes.data, 0))
+        return V
+
+    def get_state_device(self, i, V_out):
+        self._check(self.L.dg_batch_get_state(self.ctx, int(i), C.c_void_p(V_out.data_ptr()), 1))
+
+    def advance(self, n_steps):
+        self._check(self.L.dg_batch_advance(self.ctx, int(n_steps)))
+
+    def run(self, n_steps):
+        st = (_lib.Stats * self.n)()
+        self._check(self.L.dg_batch_run(self.ctx, int(n_steps), st))
+        return [_stats_dict(s) for s in st]
+
+    def stats(self):
+        st = (_lib.Stats * self.n)()
+        self._check(self.L.dg_batch_stats(self.ctx, st))
+        return [_stats_dict(s) for s in st]
+
+    def autotune(self, n_iter=10):
+        self._check(self.L.dg_batch_autotune(self.ctx, int(n_iter)))
+        return self.tiles()
+
+    def time_kernels(self, n_iter=20):
+        """Per group: average ms per launch of estep, face, volume, dt."""
+        ng = len(self.tiles())
+        ms = (C.c_double * (4 * ng))()
+        self._check(self.L.dg_batch_time_kernels(self.ctx, int(n_iter), ms, 4 * ng))
+        return [dict(zip(("estep", "face", "volume", "dt"), list(ms[4 * g:4 * g + 4]))) for g in range(ng)]
+
+    def tiles(self):
+        ng = C.c_int32()
+        self.L.dg_batch_tiles(self.ctx, None, 0, C.byref(ng))
+        out = (C.c_int32 * (3 * ng.value))()
+        self.L.dg_batch_tiles(self.ctx, out, 3 * ng.value, C.byref(ng))
+        return [list(out[3 * g:3 * g + 3]) for g in range(ng.value)]
+
+    def set_tiles(self, tiles):
+        flat = [int(t) for g in tiles for t in g]
+        arr = (C.c_int32 * len(flat))(*flat)
+        self._check(self.L.dg_batch_set_tiles(self.ctx, arr, len(flat)))
+
+    def info(self):
+        K, D, G_ = C.c_int64(), C.c_int64(), C.c_int32()
+        self._check(self.L.dg_batch_info(self.ctx, C.byref(K), C.byref(D), C.byref(G_)))
+        return dict(elements=K.value, dofs=D.value, groups=G_.value)
+
+    def launches_per_step(self):
+        return int(self.L.dg_batch_launches_per_step(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.L.dg_batch_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def batch_from_cases(cases, precision=PREC_FP64, stream=None):
+    """Batch for synthetic cases; initial states sampled at the library's own
+    node coordinates (from host-only single-instance set-ups)."""
+    specs, V0s = [], []
+    for c in cases:
+        probe = Solver(c.dim, c.coords, c.etov, c.order, c.params["reg"], c.params, face_bc=c.face_bc,
+                       bcs=c.bcs, precision=precision, allocate=False)
+        xyz = probe.node_coords()
+        probe.close()
+        V0, bed = c.initial_state(xyz)
+        specs.append(dict(dim=c.dim, coords=c.coords, etov=c.etov, order=c.order, reg=c.params["reg"],
+                          prm=c.params, face_bc=c.face_bc, bcs=c.bcs,
+                          bed=bed if c.bed_fn is not None else None))
+        V0s.append(V0)
+    b = Batch(specs, precision=precision, stream=stream)
+    for i, V0 in enumerate(V0s):
+        b.set_state(i, V0)
+    return b, V0s

@@ -74,16 +74,21 @@ _OPTIONAL_SIGS = {
     "dg_swe_implicit_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
                                            C.c_int, C.c_void_p, C.c_void_p]),
     "dg_swe_implicit_get_E": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
-    "dg_batch_init": (C.c_int, [C.c_int, C.POINTER(Mesh), C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                C.POINTER(Params), C.POINTER(C.c_void_p)]),
+    "dg_batch_init": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.POINTER(C.c_void_p)]),
     "dg_batch_workspace_size": (C.c_size_t, [C.c_void_p]),
     "dg_batch_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "dg_batch_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "dg_batch_set_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
     "dg_batch_get_state": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
-    "dg_batch_run": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(Stats)]),
-    "dg_batch_tiles": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int]),
-    "dg_batch_set_tiles": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int]),
+    "dg_batch_run": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "dg_batch_advance": (C.c_int, [C.c_void_p, C.c_int64]),
+    "dg_batch_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dg_batch_autotune": (C.c_int, [C.c_void_p, C.c_int]),
+    "dg_batch_time_kernels": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int]),
+    "dg_batch_launches_per_step": (C.c_int32, [C.c_void_p]),
+    "dg_batch_tiles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int32)]),
+    "dg_batch_set_tiles": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "dg_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "dg_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "dg_batch_destroy": (None, [C.c_void_p]),

@@ -1,0 +1,756 @@
+// Batched ensembles: many independent instances advanced by one launch per
+// (dimension, order) group and phase, replayed from a CUDA graph.
+// See include/dg_batch.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/dg_batch.h"
+#include "dg_ctx.h"
+#include "dg_kernels.cuh"
+
+using namespace dgswe;
+
+namespace {
+
+constexpr int kGraphSteps = 16;
+inline size_t a256(size_t x) { return (x + 255) & ~size_t(255); }
+
+struct Group;
+
+struct GroupDrv {
+  virtual ~GroupDrv() = default;
+  virtual void estep(dg_batch* b, Group& g, int vin, cudaStream_t s) = 0;
+  virtual void face(dg_batch* b, Group& g, int vin, cudaStream_t s) = 0;
+  virtual void volume(dg_batch* b, Group& g, int vin, int vout, double c0, double c1, cudaStream_t s) = 0;
+  virtual void dt(dg_batch* b, Group& g, cudaStream_t s) = 0;
+  virtual void mass(dg_batch* b, Group& g, int first, int count, int set_ref, cudaStream_t s) = 0;
+};
+
+struct Group {
+  int dim = 0, p = 0;
+  std::vector<int> members;          // global instance ids
+  RefOps ops;
+  int64_t K = 0, F = 0;
+  bool has_bed = false;
+  std::vector<int64_t> ebase, fbase;  // per member
+  // host staging (uploaded by set_workspace)
+  std::vector<double> geo, fn, fsj, face_n, face_sj, bed;
+  std::vector<int32_t> nbr, fid, fe1, fe2, inst, gid;
+  std::vector<int8_t> nbrf, ff1, ff2;
+  std::vector<int64_t> ebeg;
+  struct {
+    size_t geo, nbr, nbrf, fid, fn, fsj, fe1, fe2, ff1, ff2, fnrm, fsjf, bed, inst, ebeg, gid, V[3], E, wflux, wint,
+        blk_e, blk_gid, mblk, partial;
+  } off{};
+  std::vector<int64_t> blk_e;      // step-size blocks: element ranges (n_blk + 1)
+  std::vector<int32_t> blk_gid;    // global instance of each block
+  std::vector<int32_t> mblk;       // first block of each member (members + 1)
+  int tile[3] = {128, 128, 128};
+  std::unique_ptr<GroupDrv> drv;
+};
+
+}  // namespace
+
+struct dg_batch {
+  int n = 0, prec = 0;
+  size_t rsize = 8;
+  std::vector<int> dim, order, reg, group_of, local_of;
+  std::vector<int64_t> K_of, Np_of;
+  std::vector<dg_swe_params> prm;
+  std::vector<Group> groups;
+  std::vector<int> bc_base;
+  int n_bc_total = 0;
+  std::vector<char> h_phys, h_bc;  // host copies of the per-instance tables
+  std::vector<double> h_iparm;     // per instance: g_c, h_floor, cfl, nu
+  size_t ws_need = 0;
+  char* ws = nullptr;
+  size_t off_ptab = 0, off_bct = 0, off_sc = 0, off_iparm = 0;
+  cudaStream_t stream = nullptr, priv = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaGraphExec_t g1 = nullptr, gN = nullptr;
+  std::string err;
+  template <typename T>
+  T* at(size_t o) const { return reinterpret_cast<T*>(ws + o); }
+};
+
+namespace {
+
+dg_status bfail(dg_batch* b, dg_status s, const std::string& m) {
+  if (b) b->err = m;
+  return s;
+}
+dg_status bcuda(dg_batch* b, cudaError_t e, const char* where) {
+  return bfail(b, DG_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define BK(call)                                         \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return bcuda(b, e_, #call);   \
+  } while (0)
+
+template <int DIM, int P, typename R>
+struct GDrv final : GroupDrv {
+  using S = Sh<DIM, P>;
+  EstepOps<DIM, P, R> eo{};
+  FaceOps<DIM, P, R> fo{};
+  VolOps<DIM, P, R> vo{};
+  explicit GDrv(const RefOps& o) { fill_ops<DIM, P, R>(o, eo, fo, vo); }
+
+  const Phys<R>* ptab(dg_batch* b) { return b->at<Phys<R>>(b->off_ptab); }
+  const BCEntry<R>* bct(dg_batch* b) { return b->at<BCEntry<R>>(b->off_bct); }
+
+  void estep(dg_batch* b, Group& g, int vin, cudaStream_t s) override {
+    const int K = (int)g.K, T = g.tile[0];
+    estep_kernel<DIM, P, R><<<(K + T - 1) / T, T, 0, s>>>(
+        K, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<R>(g.off.geo), b->at<int32_t>(g.off.nbr),
+        b->at<int8_t>(g.off.nbrf), b->at<R>(g.off.fn), b->at<R>(g.off.fsj), eo, bct(b));
+  }
+  void face(dg_batch* b, Group& g, int vin, cudaStream_t s) override {
+    const int K = (int)g.K, F = (int)g.F, T = g.tile[1];
+    const long long n = (long long)F * S::NFQ;
+    face_kernel<DIM, P, R, true><<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
+        K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<int32_t>(g.off.fe1), b->at<int8_t>(g.off.ff1),
+        b->at<int32_t>(g.off.fe2), b->at<int8_t>(g.off.ff2), b->at<R>(g.off.fnrm), b->at<R>(g.off.fsjf),
+        b->at<R>(g.off.wflux), fo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), bct(b));
+  }
+  void volume(dg_batch* b, Group& g, int vin, int vout, double c0, double c1, cudaStream_t s) override {
+    const int K = (int)g.K, F = (int)g.F, T = g.tile[2];
+    volume_kernel<DIM, P, R, true><<<(K + T - 1) / T, T, 0, s>>>(
+        K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.V[0]), b->at<R>(g.off.V[vout]), b->at<R>(g.off.E),
+        g.has_bed ? b->at<R>(g.off.bed) : nullptr, b->at<R>(g.off.geo), b->at<int32_t>(g.off.fid),
+        b->at<R>(g.off.wflux), vo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), 1, (R)c0, (R)c1,
+        b->at<DevScalars>(b->off_sc));
+  }
+  void dt(dg_batch* b, Group& g, cudaStream_t s) override {
+    const int nblk = (int)g.blk_gid.size(), nm = (int)g.members.size();
+    dt_block_kernel<DIM, P, R><<<nblk, 256, 0, s>>>((int)g.K, b->at<int64_t>(g.off.blk_e),
+                                                    b->at<int32_t>(g.off.blk_gid), b->at<R>(g.off.V[0]),
+                                                    b->at<R>(g.off.geo), b->at<double>(b->off_iparm),
+                                                    b->at<double>(g.off.partial));
+    dt_members_kernel<<<(nm + 7) / 8, 256, 0, s>>>(nm, b->at<int32_t>(g.off.mblk), b->at<int32_t>(g.off.gid),
+                                                   b->at<double>(g.off.partial), b->at<DevScalars>(b->off_sc));
+  }
+  void mass(dg_batch* b, Group& g, int first, int count, int set_ref, cudaStream_t s) override {
+    mass_instance_kernel<S::NP, R><<<(unsigned)count, 256, 0, s>>>(
+        (int)g.K, b->at<int64_t>(g.off.ebeg) + first, b->at<int32_t>(g.off.gid) + first, b->at<R>(g.off.V[0]),
+        b->at<R>(g.off.geo), b->at<double>(g.off.wint), set_ref, b->at<DevScalars>(b->off_sc));
+  }
+};
+
+template <typename R>
+std::unique_ptr<GroupDrv> make_gdrv(int dim, int p, const RefOps& o) {
+#define GCASE(D, PP) \
+  if (dim == D && p == PP) return std::unique_ptr<GroupDrv>(new GDrv<D, PP, R>(o));
+  GCASE(1, 1) GCASE(1, 2) GCASE(1, 3) GCASE(2, 1) GCASE(2, 2) GCASE(2, 3)
+#undef GCASE
+  return nullptr;
+}
+
+void enqueue_step(dg_batch* b, cudaStream_t s) {
+  for (auto& g : b->groups) g.drv->dt(b, g, s);
+  const int vin[3] = {0, 1, 2}, vout[3] = {1, 2, 0};
+  const double c0[3] = {0.0, 0.75, 1.0 / 3.0}, c1[3] = {1.0, 0.25, 2.0 / 3.0};
+  for (int st = 0; st < 3; ++st)
+    for (auto& g : b->groups) {
+      g.drv->estep(b, g, vin[st], s);
+      g.drv->face(b, g, vin[st], s);
+      g.drv->volume(b, g, vin[st], vout[st], c0[st], c1[st], s);
+    }
+}
+
+void destroy_graphs(dg_batch* b) {
+  if (b->g1) cudaGraphExecDestroy(b->g1);
+  if (b->gN) cudaGraphExecDestroy(b->gN);
+  b->g1 = b->gN = nullptr;
+}
+
+dg_status capture(dg_batch* b, int nsteps, cudaGraphExec_t* out) {
+  cudaGraph_t g = nullptr;
+  BK(cudaStreamBeginCapture(b->priv, cudaStreamCaptureModeThreadLocal));
+  for (int i = 0; i < nsteps; ++i) enqueue_step(b, b->priv);
+  cudaError_t e = cudaStreamEndCapture(b->priv, &g);
+  if (e != cudaSuccess) return bcuda(b, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bcuda(b, e, "cudaGraphInstantiate");
+  return DG_OK;
+}
+
+template <typename R>
+void push_phys(const dg_swe_params& p, int reg, std::vector<char>& out) {
+  Phys<R> ph{};
+  ph.gc = (R)(p.g * std::cos(p.alpha));
+  ph.gs = (R)(p.g * std::sin(p.alpha));
+  ph.rho_inv = (R)(1.0 / p.rho);
+  ph.eta = (R)p.eta;
+  ph.sigma0 = (R)p.sigma0;
+  ph.gamma = (R)p.gamma;
+  ph.beta = (R)p.beta;
+  ph.pap_m = (R)p.pap_m;
+  ph.h_floor = (R)p.h_floor;
+  ph.reg = reg;
+  const char* c = reinterpret_cast<const char*>(&ph);
+  out.insert(out.end(), c, c + sizeof(ph));
+}
+
+template <typename R>
+void push_bc(const dg_swe_bc& bc, std::vector<char>& out) {
+  BCEntry<R> e{};
+  for (int s = 0; s < 7; ++s) {
+    e.mode[s] = bc.mode[s];
+    e.val[s] = (R)bc.value[s];
+  }
+  const char* c = reinterpret_cast<const char*>(&e);
+  out.insert(out.end(), c, c + sizeof(e));
+}
+
+dg_status check(dg_batch* b) {
+  if (!b) return DG_ERR_ARG;
+  if (!b->ws) return bfail(b, DG_ERR_WORKSPACE, "no workspace set (dg_batch_set_workspace)");
+  return DG_OK;
+}
+
+template <typename Rin, typename Rout>
+void conv(const void* in, void* out, size_t n, cudaStream_t s) {
+  if (n) convert_kernel<Rin, Rout><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, (const Rin*)in, (Rout*)out);
+}
+
+dg_status read_stats(dg_batch* b, dg_swe_stats* st) {
+  std::vector<DevScalars> h(b->n);
+  BK(cudaMemcpyAsync(h.data(), b->at<DevScalars>(b->off_sc), b->n * sizeof(DevScalars), cudaMemcpyDeviceToHost,
+                     b->stream));
+  BK(cudaStreamSynchronize(b->stream));
+  int bad = -1;
+  for (int i = 0; i < b->n; ++i) {
+    if (h[i].status && bad < 0) bad = i;
+    if (!st) continue;
+    st[i].steps = h[i].steps;
+    st[i].t = h[i].t;
+    st[i].dt_last = h[i].dt;
+    st[i].dt_min = h[i].steps ? h[i].dt_min : 0.0;
+    st[i].dt_max = h[i].dt_max;
+    st[i].mass = h[i].mass;
+    st[i].mass0 = h[i].mass0;
+    st[i].status = h[i].status;
+  }
+  if (bad >= 0) return bfail(b, (dg_status)h[bad].status, "device status: non-finite state in instance " + std::to_string(bad));
+  return DG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, const int* regs,
+                        const dg_swe_params* params, dg_batch** out) {
+  if (!out) return DG_ERR_ARG;
+  *out = nullptr;
+  std::unique_ptr<dg_batch> b(new dg_batch());
+  if (n < 1 || !meshes || !orders || !regs || !params) {
+    *out = b.release();
+    return bfail(*out, DG_ERR_ARG, "need n >= 1 and non-null arrays");
+  }
+  b->n = n;
+  b->prec = params[0].precision;
+  b->rsize = b->prec == DG_PREC_FP64 ? 8 : 4;
+  std::map<std::pair<int, int>, int> gidx;
+  b->group_of.assign(n, -1);
+  b->local_of.assign(n, -1);
+  b->K_of.assign(n, 0);
+  b->Np_of.assign(n, 0);
+  b->bc_base.assign(n, 0);
+  std::vector<char> phys_bytes, bc_bytes;
+  std::vector<double> iparm;
+  for (int i = 0; i < n; ++i) {
+    if (params[i].precision != b->prec) {
+      *out = b.release();
+      return bfail(*out, DG_ERR_ARG, "instance " + std::to_string(i) + ": all instances need the same precision");
+    }
+    // validate and build through the single-instance setup (host only)
+    dg_swe_ctx* c = nullptr;
+    dg_status st = dg_swe_init(&meshes[i], orders[i], regs[i], &params[i], &c);
+    if (st != DG_OK) {
+      std::string m = c ? dg_swe_last_error(c) : "";
+      dg_swe_destroy(c);
+      *out = b.release();
+      return bfail(*out, st, "instance " + std::to_string(i) + ": " + m);
+    }
+    b->dim.push_back(c->dim);
+    b->order.push_back(c->p);
+    b->reg.push_back(c->reg);
+    b->prm.push_back(params[i]);
+    auto key = std::make_pair(c->dim, c->p);
+    if (!gidx.count(key)) {
+      gidx[key] = (int)b->groups.size();
+      b->groups.emplace_back();
+      Group& g = b->groups.back();
+      g.dim = c->dim;
+      g.p = c->p;
+      g.ops = c->ops;
+      g.drv = b->prec == DG_PREC_FP64 ? make_gdrv<double>(g.dim, g.p, g.ops) : make_gdrv<float>(g.dim, g.p, g.ops);
+    }
+    const int gi = gidx[key];
+    Group& g = b->groups[gi];
+    b->group_of[i] = gi;
+    b->local_of[i] = (int)g.members.size();
+    b->K_of[i] = c->mesh.K;
+    b->Np_of[i] = c->ops.Np;
+    b->bc_base[i] = b->n_bc_total;
+    b->n_bc_total += params[i].n_bc;
+    g.members.push_back(i);
+    g.ebase.push_back(g.K);
+    g.fbase.push_back(g.F);
+    // append this instance's mesh to the group (SoA over the group)
+    const MeshData& m = c->mesh;
+    const int64_t K = m.K, F = m.F, eb = g.K, fb = g.F;
+    const int nf = c->dim + 1, Np = c->ops.Np;
+    auto remap_nbr = [&](int32_t v) -> int32_t {
+      return v >= 0 ? (int32_t)(v + eb) : (int32_t)(-1 - (b->bc_base[i] + (-1 - v)));
+    };
+    // element-face arrays: [nf][K] per instance -> [nf][Kg] (rebuilt below)
+    g.K += K;
+    g.F += F;
+    g.inst.insert(g.inst.end(), (size_t)K, (int32_t)i);
+    g.gid.push_back(i);
+    // per-member SoA blocks, interleaved into group SoA arrays below
+    g.geo.insert(g.geo.end(), m.geo.begin(), m.geo.end());            // [6][K] blocks, interleaved later
+    for (int64_t k = 0; k < nf * K; ++k) g.nbr.push_back(remap_nbr(m.nbr[k]));
+    g.nbrf.insert(g.nbrf.end(), m.nbrf.begin(), m.nbrf.end());
+    for (int64_t k = 0; k < nf * K; ++k) {
+      uint32_t raw = (uint32_t)m.fid[k];
+      uint32_t id = (raw & 0x7fffffffu) + (uint32_t)fb;
+      g.fid.push_back((int32_t)(id | (raw & 0x80000000u)));
+    }
+    g.fn.insert(g.fn.end(), m.fn.begin(), m.fn.end());
+    g.fsj.insert(g.fsj.end(), m.fsj.begin(), m.fsj.end());
+    for (int64_t f = 0; f < F; ++f) {
+      g.fe1.push_back((int32_t)(m.face_e1[f] + eb));
+      g.fe2.push_back(remap_nbr(m.face_e2[f]));
+    }
+    g.ff1.insert(g.ff1.end(), m.face_f1.begin(), m.face_f1.end());
+    g.ff2.insert(g.ff2.end(), m.face_f2.begin(), m.face_f2.end());
+    g.face_n.insert(g.face_n.end(), m.face_n.begin(), m.face_n.end());
+    g.face_sj.insert(g.face_sj.end(), m.face_sj.begin(), m.face_sj.end());
+    if (c->has_bed) {
+      if (!g.has_bed) {
+        g.bed.assign((size_t)(eb)*Np, 0.0);
+        g.has_bed = true;
+      }
+      g.bed.insert(g.bed.end(), c->bed.begin(), c->bed.end());
+    } else if (g.has_bed) {
+      g.bed.insert(g.bed.end(), (size_t)K * Np, 0.0);
+    }
+    // per-instance tables
+    if (b->rsize == 8) push_phys<double>(params[i], regs[i], phys_bytes);
+    else push_phys<float>(params[i], regs[i], phys_bytes);
+    for (int k = 0; k < params[i].n_bc; ++k) {
+      if (b->rsize == 8) push_bc<double>(params[i].bc[k], bc_bytes);
+      else push_bc<float>(params[i].bc[k], bc_bytes);
+    }
+    const auto& pp = params[i];
+    iparm.push_back(pp.g * std::cos(pp.alpha));
+    iparm.push_back(pp.h_floor);
+    iparm.push_back(pp.cfl);
+    iparm.push_back((4.0 * pp.eta + max_bingham_slope(regs[i], pp.sigma0, pp.gamma, pp.pap_m)) / pp.rho);
+    dg_swe_destroy(c);
+  }
+  // interleave per-member SoA blocks into group SoA arrays
+  for (auto& g : b->groups) {
+    const int nf = g.dim + 1, dim = g.dim;
+    const int64_t Kg = g.K, Fg = g.F;
+    std::vector<double> geo(6 * Kg), fn((size_t)nf * dim * Kg), fsj(nf * Kg), fnm((size_t)dim * Fg);
+    std::vector<int32_t> nbr(nf * Kg), fid(nf * Kg);
+    std::vector<int8_t> nbrf(nf * Kg);
+    size_t pg = 0, pn = 0, pfn = 0, pfs = 0, pfnm = 0;
+    for (size_t mi = 0; mi < g.members.size(); ++mi) {
+      const int64_t eb = g.ebase[mi], fb = g.fbase[mi];
+      const int64_t K = (mi + 1 < g.members.size() ? g.ebase[mi + 1] : Kg) - eb;
+      const int64_t F = (mi + 1 < g.members.size() ? g.fbase[mi + 1] : Fg) - fb;
+      for (int c = 0; c < 6; ++c)
+        for (int64_t e = 0; e < K; ++e) geo[c * Kg + eb + e] = g.geo[pg + c * K + e];
+      pg += 6 * K;
+      for (int f = 0; f < nf; ++f)
+        for (int64_t e = 0; e < K; ++e) {
+          nbr[f * Kg + eb + e] = g.nbr[pn + f * K + e];
+          nbrf[f * Kg + eb + e] = g.nbrf[pn + f * K + e];
+          fid[f * Kg + eb + e] = g.fid[pn + f * K + e];
+          fsj[f * Kg + eb + e] = g.fsj[pfs + f * K + e];
+          for (int d = 0; d < dim; ++d) fn[(f * dim + d) * Kg + eb + e] = g.fn[pfn + (f * dim + d) * K + e];
+        }
+      pn += nf * K;
+      pfs += nf * K;
+      pfn += (size_t)nf * dim * K;
+      for (int d = 0; d < dim; ++d)
+        for (int64_t f = 0; f < F; ++f) fnm[d * Fg + fb + f] = g.face_n[pfnm + d * F + f];
+      pfnm += (size_t)dim * F;
+    }
+    g.geo.swap(geo);
+    g.fn.swap(fn);
+    g.fsj.swap(fsj);
+    g.face_n.swap(fnm);
+    g.nbr.swap(nbr);
+    g.nbrf.swap(nbrf);
+    g.fid.swap(fid);
+    g.ebeg = g.ebase;
+    g.ebeg.push_back(Kg);
+    g.blk_e.clear();
+    g.blk_gid.clear();
+    g.mblk.clear();
+    for (size_t mi = 0; mi < g.members.size(); ++mi) {
+      g.mblk.push_back((int32_t)g.blk_gid.size());
+      for (int64_t e = g.ebeg[mi]; e < g.ebeg[mi + 1]; e += 256) {
+        g.blk_e.push_back(e);
+        g.blk_gid.push_back(g.members[mi]);
+      }
+    }
+    g.mblk.push_back((int32_t)g.blk_gid.size());
+    g.blk_e.push_back(Kg);
+    if (g.K > 0x7fffffff / 16 || g.F > 0x7fffffff / 8) {
+      *out = b.release();
+      return bfail(*out, DG_ERR_ARG, "group too large for 32-bit indexing");
+    }
+  }
+  // workspace layout
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o += a256(bytes);
+    return r;
+  };
+  const size_t rs = b->rsize;
+  for (auto& g : b->groups) {
+    const int64_t K = g.K, F = g.F;
+    const int nf = g.dim + 1, Np = g.ops.Np, nV = g.dim + 1, nE = g.dim * g.dim;
+    g.off.geo = take(6 * K * rs);
+    g.off.nbr = take(nf * K * 4);
+    g.off.nbrf = take(nf * K);
+    g.off.fid = take(nf * K * 4);
+    g.off.fn = take((size_t)nf * g.dim * K * rs);
+    g.off.fsj = take(nf * K * rs);
+    g.off.fe1 = take(F * 4);
+    g.off.fe2 = take(F * 4);
+    g.off.ff1 = take(F);
+    g.off.ff2 = take(F);
+    g.off.fnrm = take((size_t)g.dim * F * rs);
+    g.off.fsjf = take(F * rs);
+    g.off.bed = take(g.has_bed ? K * Np * rs : 0);
+    g.off.inst = take(K * 4);
+    g.off.ebeg = take(g.ebeg.size() * 8);
+    g.off.gid = take(g.gid.size() * 4);
+    for (int v = 0; v < 3; ++v) g.off.V[v] = take((size_t)nV * K * Np * rs);
+    g.off.E = take((size_t)nE * K * Np * rs);
+    g.off.wflux = take((size_t)nV * F * g.ops.Nfq * rs);
+    g.off.wint = take(Np * 8);
+    g.off.blk_e = take(g.blk_e.size() * 8);
+    g.off.blk_gid = take(g.blk_gid.size() * 4);
+    g.off.mblk = take(g.mblk.size() * 4);
+    g.off.partial = take(g.blk_gid.size() * 8);
+  }
+  b->off_ptab = take(phys_bytes.size());
+  b->off_bct = take(bc_bytes.size());
+  b->off_sc = take((size_t)n * sizeof(DevScalars));
+  b->off_iparm = take(iparm.size() * 8);
+  b->ws_need = o;
+  b->h_phys = std::move(phys_bytes);
+  b->h_bc = std::move(bc_bytes);
+  b->h_iparm = std::move(iparm);
+  *out = b.release();
+  return DG_OK;
+}
+
+size_t dg_batch_workspace_size(const dg_batch* b) { return b ? b->ws_need : 0; }
+
+dg_status dg_batch_set_stream(dg_batch* b, void* s) {
+  if (!b) return DG_ERR_ARG;
+  b->stream = (cudaStream_t)s;
+  return DG_OK;
+}
+
+dg_status dg_batch_set_workspace(dg_batch* b, void* ptr, size_t bytes) {
+  if (!b) return DG_ERR_ARG;
+  if (!ptr || bytes < b->ws_need) return bfail(b, DG_ERR_WORKSPACE, "workspace missing or smaller than dg_batch_workspace_size()");
+  if (((uintptr_t)ptr & 255) != 0) return bfail(b, DG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+  destroy_graphs(b);
+  b->ws = (char*)ptr;
+  cudaStream_t s = b->stream;
+  auto up = [&](size_t off, const void* src, size_t n) -> cudaError_t {
+    return n ? cudaMemcpyAsync(b->ws + off, src, n, cudaMemcpyHostToDevice, s) : cudaSuccess;
+  };
+  auto upr = [&](size_t off, const std::vector<double>& v) -> cudaError_t {
+    if (v.empty()) return cudaSuccess;
+    if (b->rsize == 8) return up(off, v.data(), v.size() * 8);
+    std::vector<float> f(v.begin(), v.end());
+    cudaError_t e = up(off, f.data(), f.size() * 4);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e;
+  };
+  for (auto& g : b->groups) {
+    BK(upr(g.off.geo, g.geo));
+    BK(up(g.off.nbr, g.nbr.data(), g.nbr.size() * 4));
+    BK(up(g.off.nbrf, g.nbrf.data(), g.nbrf.size()));
+    BK(up(g.off.fid, g.fid.data(), g.fid.size() * 4));
+    BK(upr(g.off.fn, g.fn));
+    BK(upr(g.off.fsj, g.fsj));
+    BK(up(g.off.fe1, g.fe1.data(), g.fe1.size() * 4));
+    BK(up(g.off.fe2, g.fe2.data(), g.fe2.size() * 4));
+    BK(up(g.off.ff1, g.ff1.data(), g.ff1.size()));
+    BK(up(g.off.ff2, g.ff2.data(), g.ff2.size()));
+    BK(upr(g.off.fnrm, g.face_n));
+    BK(upr(g.off.fsjf, g.face_sj));
+    if (g.has_bed) BK(upr(g.off.bed, g.bed));
+    BK(up(g.off.inst, g.inst.data(), g.inst.size() * 4));
+    BK(up(g.off.ebeg, g.ebeg.data(), g.ebeg.size() * 8));
+    BK(up(g.off.gid, g.gid.data(), g.gid.size() * 4));
+    BK(up(g.off.wint, g.ops.wint.data(), g.ops.wint.size() * 8));
+    BK(up(g.off.blk_e, g.blk_e.data(), g.blk_e.size() * 8));
+    BK(up(g.off.blk_gid, g.blk_gid.data(), g.blk_gid.size() * 4));
+    BK(up(g.off.mblk, g.mblk.data(), g.mblk.size() * 4));
+    BK(cudaMemsetAsync(b->ws + g.off.E, 0, (size_t)g.dim * g.dim * g.K * g.ops.Np * b->rsize, s));
+    for (int v = 0; v < 3; ++v)
+      BK(cudaMemsetAsync(b->ws + g.off.V[v], 0, (size_t)(g.dim + 1) * g.K * g.ops.Np * b->rsize, s));
+  }
+  BK(up(b->off_ptab, b->h_phys.data(), b->h_phys.size()));
+  BK(up(b->off_bct, b->h_bc.data(), b->h_bc.size()));
+  BK(up(b->off_iparm, b->h_iparm.data(), b->h_iparm.size() * 8));
+  reset_scalars_array_kernel<<<(b->n + 127) / 128, 128, 0, s>>>(b->n, b->at<DevScalars>(b->off_sc));
+  BK(cudaGetLastError());
+  BK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+dg_status dg_batch_set_state(dg_batch* b, int i, const double* V, int on_device) {
+  dg_status st = check(b);
+  if (st != DG_OK) return st;
+  if (i < 0 || i >= b->n || !V) return bfail(b, DG_ERR_ARG, "bad instance index or null state");
+  Group& g = b->groups[b->group_of[i]];
+  const int mi = b->local_of[i];
+  const int64_t K = b->K_of[i], Np = b->Np_of[i], eb = g.ebase[mi];
+  const int nV = g.dim + 1;
+  cudaStream_t s = b->stream;
+  for (int f = 0; f < nV; ++f) {
+    char* dst = b->ws + g.off.V[0] + ((size_t)f * g.K + eb) * Np * b->rsize;
+    const double* src = V + (size_t)f * K * Np;
+    if (b->rsize == 8) {
+      BK(cudaMemcpyAsync(dst, src, K * Np * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    } else if (on_device) {
+      conv<double, float>(src, dst, K * Np, s);
+    } else {
+      std::vector<float> h(src, src + K * Np);
+      BK(cudaMemcpyAsync(dst, h.data(), h.size() * 4, cudaMemcpyHostToDevice, s));
+      BK(cudaStreamSynchronize(s));
+    }
+  }
+  reset_scalars_array_kernel<<<1, 1, 0, s>>>(1, b->at<DevScalars>(b->off_sc) + i);
+  g.drv->mass(b, g, mi, 1, 1, s);
+  BK(cudaGetLastError());
+  if (!on_device) BK(cudaStreamSynchronize(s));
+  return DG_OK;
+}
+
+dg_status dg_batch_get_state(dg_batch* b, int i, double* V, int on_device) {
+  dg_status st = check(b);
+  if (st != DG_OK) return st;
+  if (i < 0 || i >= b->n || !V) return bfail(b, DG_ERR_ARG, "bad instance index or null output");
+  Group& g = b->groups[b->group_of[i]];
+  const int mi = b->local_of[i];
+  const int64_t K = b->K_of[i], Np = b->Np_of[i], eb = g.ebase[mi];
+  const int nV = g.dim + 1;
+  cudaStream_t s = b->stream;
+  for (int f = 0; f < nV; ++f) {
+    const char* src = b->ws + g.off.V[0] + ((size_t)f * g.K + eb) * Np * b->rsize;
+    double* dst = V + (size_t)f * K * Np;
+    if (b->rsize == 8) {
+      BK(cudaMemcpyAsync(dst, src, K * Np * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    } else if (on_device) {
+      conv<float, double>(src, dst, K * Np, s);
+    } else {
+      std::vector<float> h(K * Np);
+      BK(cudaMemcpyAsync(h.data(), src, h.size() * 4, cudaMemcpyDeviceToHost, s));
+      BK(cudaStreamSynchronize(s));
+      for (size_t k = 0; k < h.size(); ++k) dst[k] = h[k];
+    }
+  }
+  BK(cudaGetLastError());
+  return read_stats(b, nullptr);
+}
+
+dg_status dg_batch_advance(dg_batch* b, int64_t n_steps) {
+  dg_status st = check(b);
+  if (st != DG_OK) return st;
+  if (n_steps < 0) return bfail(b, DG_ERR_ARG, "n_steps < 0");
+  if (n_steps == 0) return DG_OK;
+  if (!b->priv) {
+    BK(cudaStreamCreateWithFlags(&b->priv, cudaStreamNonBlocking));
+    BK(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+    BK(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming));
+  }
+  if (!b->g1) {
+    st = capture(b, 1, &b->g1);
+    if (st != DG_OK) return st;
+    st = capture(b, kGraphSteps, &b->gN);
+    if (st != DG_OK) return st;
+  }
+  BK(cudaEventRecord(b->ev_fork, b->stream));
+  BK(cudaStreamWaitEvent(b->priv, b->ev_fork, 0));
+  int64_t left = n_steps;
+  while (left >= kGraphSteps) {
+    BK(cudaGraphLaunch(b->gN, b->priv));
+    left -= kGraphSteps;
+  }
+  while (left-- > 0) BK(cudaGraphLaunch(b->g1, b->priv));
+  BK(cudaEventRecord(b->ev_join, b->priv));
+  BK(cudaStreamWaitEvent(b->stream, b->ev_join, 0));
+  return DG_OK;
+}
+
+dg_status dg_batch_stats(dg_batch* b, dg_swe_stats* stats) {
+  dg_status st = check(b);
+  if (st != DG_OK) return st;
+  for (auto& g : b->groups) g.drv->mass(b, g, 0, (int)g.members.size(), 0, b->stream);
+  BK(cudaGetLastError());
+  return read_stats(b, stats);
+}
+
+dg_status dg_batch_run(dg_batch* b, int64_t n_steps, dg_swe_stats* stats) {
+  dg_status st = dg_batch_advance(b, n_steps);
+  if (st != DG_OK) return st;
+  return dg_batch_stats(b, stats);
+}
+
+dg_status dg_batch_autotune(dg_batch* b, int n_iter) {
+  dg_status st = check(b);
+  if (st != DG_OK) return st;
+  if (n_iter < 1) return bfail(b, DG_ERR_ARG, "n_iter >= 1");
+  static const int cand[4] = {32, 64, 128, 256};
+  cudaStream_t s = b->stream;
+  cudaEvent_t e0, e1;
+  BK(cudaEventCreate(&e0));
+  BK(cudaEventCreate(&e1));
+  // the step-size scalars are left as they are: the volume pass below writes
+  // stage buffer 1 from buffer 0 and leaves the state untouched
+  for (auto& g : b->groups) {
+    g.drv->estep(b, g, 0, s);
+    g.drv->face(b, g, 0, s);
+    for (int k = 0; k < 3; ++k) {
+      float best = 1e30f;
+      int best_t = g.tile[k];
+      for (int ci = 0; ci < 4; ++ci) {
+        g.tile[k] = cand[ci];
+        auto launch = [&]() {
+          if (k == 0) g.drv->estep(b, g, 0, s);
+          else if (k == 1) g.drv->face(b, g, 0, s);
+          else g.drv->volume(b, g, 0, 1, 0.0, 1.0, s);
+        };
+        launch();  // warm-up
+        BK(cudaEventRecord(e0, s));
+        for (int it = 0; it < n_iter; ++it) launch();
+        BK(cudaEventRecord(e1, s));
+        BK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        BK(cudaEventElapsedTime(&ms, e0, e1));
+        BK(cudaGetLastError());
+        if (ms < best) {
+          best = ms;
+          best_t = cand[ci];
+        }
+      }
+      g.tile[k] = best_t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  destroy_graphs(b);
+  return DG_OK;
+}
+
+dg_status dg_batch_time_kernels(dg_batch* b, int n_iter, double* ms, int cap) {
+  dg_status st = check(b);
+  if (st != DG_OK) return st;
+  if (n_iter < 1 || !ms || cap < 4 * (int)b->groups.size()) return bfail(b, DG_ERR_ARG, "need n_iter >= 1 and 4 slots per group");
+  cudaStream_t s = b->stream;
+  cudaEvent_t e0, e1;
+  BK(cudaEventCreate(&e0));
+  BK(cudaEventCreate(&e1));
+  std::vector<DevScalars> saved(b->n);
+  BK(cudaMemcpyAsync(saved.data(), b->at<DevScalars>(b->off_sc), b->n * sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+  BK(cudaStreamSynchronize(s));
+  for (size_t gi = 0; gi < b->groups.size(); ++gi) {
+    Group& g = b->groups[gi];
+    g.drv->estep(b, g, 0, s);
+    g.drv->face(b, g, 0, s);
+    for (int k = 0; k < 4; ++k) {
+      BK(cudaEventRecord(e0, s));
+      for (int it = 0; it < n_iter; ++it) {
+        if (k == 0) g.drv->estep(b, g, 0, s);
+        else if (k == 1) g.drv->face(b, g, 0, s);
+        else if (k == 2) g.drv->volume(b, g, 0, 1, 0.0, 1.0, s);
+        else g.drv->dt(b, g, s);
+      }
+      BK(cudaEventRecord(e1, s));
+      BK(cudaEventSynchronize(e1));
+      float t = 0.f;
+      BK(cudaEventElapsedTime(&t, e0, e1));
+      ms[4 * gi + k] = (double)t / n_iter;
+    }
+  }
+  // the dt kernel advanced t and the step counters: restore them
+  BK(cudaMemcpyAsync(b->at<DevScalars>(b->off_sc), saved.data(), b->n * sizeof(DevScalars), cudaMemcpyHostToDevice, s));
+  BK(cudaStreamSynchronize(s));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  BK(cudaGetLastError());
+  return DG_OK;
+}
+
+dg_status dg_batch_tiles(const dg_batch* b, int32_t* out, int cap, int32_t* n_groups) {
+  if (!b) return DG_ERR_ARG;
+  if (n_groups) *n_groups = (int32_t)b->groups.size();
+  if (out)
+    for (size_t g = 0; g < b->groups.size(); ++g)
+      for (int k = 0; k < 3; ++k)
+        if ((int)(3 * g + k) < cap) out[3 * g + k] = b->groups[g].tile[k];
+  return DG_OK;
+}
+
+dg_status dg_batch_set_tiles(dg_batch* b, const int32_t* tiles, int n) {
+  if (!b || !tiles || n != 3 * (int)b->groups.size()) return bfail(b, DG_ERR_ARG, "need 3 block sizes per group");
+  for (int i = 0; i < n; ++i)
+    if (tiles[i] < 32 || tiles[i] > 256 || tiles[i] % 32) return bfail(b, DG_ERR_ARG, "block sizes must be 32..256, multiples of 32");
+  for (size_t g = 0; g < b->groups.size(); ++g)
+    for (int k = 0; k < 3; ++k) b->groups[g].tile[k] = tiles[3 * g + k];
+  destroy_graphs(b);
+  return DG_OK;
+}
+
+dg_status dg_batch_info(const dg_batch* b, int64_t* elements, int64_t* dofs, int32_t* n_groups) {
+  if (!b) return DG_ERR_ARG;
+  int64_t K = 0, D = 0;
+  for (int i = 0; i < b->n; ++i) {
+    K += b->K_of[i];
+    D += b->K_of[i] * b->Np_of[i] * (b->dim[i] + 1);
+  }
+  if (elements) *elements = K;
+  if (dofs) *dofs = D;
+  if (n_groups) *n_groups = (int32_t)b->groups.size();
+  return DG_OK;
+}
+
+int32_t dg_batch_launches_per_step(const dg_batch* b) { return b ? (int32_t)(11 * b->groups.size()) : 0; }
+
+const char* dg_batch_last_error(const dg_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+void dg_batch_destroy(dg_batch* b) {
+  if (!b) return;
+  destroy_graphs(b);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->priv) cudaStreamDestroy(b->priv);
+  delete b;
+}
+
+}  // extern "C"

@@ -25,6 +25,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dg_host.h"
+
 namespace dgswe {
 
 template <int DIM, int P>
@@ -39,12 +41,21 @@ struct Sh {
   static constexpr int NE = DIM * DIM;
 };
 
+// Physical parameters of one instance (kernel parameter for a single
+// context, a per-instance device table for a batch).
 template <typename R>
 struct Phys {
   R gc, gs, rho_inv, eta, sigma0, gamma, beta, pap_m, h_floor;
   int reg;
-  int bc_mode[8][7];
-  R bc_val[8][7];
+};
+
+// One boundary descriptor: per slot (V fields then E fields) a mode
+// (0 copy, 1 Dirichlet, 2 wall) and a Dirichlet value.  Boundary faces carry
+// -1 - (index into a device table of these).
+template <typename R>
+struct BCEntry {
+  int mode[7];
+  R val[7];
 };
 
 template <int DIM, int P, typename R>
@@ -148,12 +159,12 @@ __device__ __forceinline__ void stress(const R* E, const Phys<R>& ph, R sig[DIM]
 
 // Exterior state at a boundary face point (Sec. 5.2 ghost values).
 template <int DIM, typename R>
-__device__ __forceinline__ void ghost_V(const R* Vm, const R* n, int bc, const Phys<R>& ph, R* Vp) {
+__device__ __forceinline__ void ghost_V(const R* Vm, const R* n, const BCEntry<R>& b, R* Vp) {
   bool wall = false;
 #pragma unroll
   for (int v = 0; v < DIM + 1; ++v) {
-    int md = ph.bc_mode[bc][v];
-    Vp[v] = md == 1 ? ph.bc_val[bc][v] : Vm[v];
+    int md = b.mode[v];
+    Vp[v] = md == 1 ? b.val[v] : Vm[v];
     if (v > 0 && md == 2) wall = true;
   }
   if (wall) {
@@ -166,11 +177,11 @@ __device__ __forceinline__ void ghost_V(const R* Vm, const R* n, int bc, const P
 }
 
 template <int DIM, typename R>
-__device__ __forceinline__ void ghost_E(const R* Em, int bc, const Phys<R>& ph, R* Ep) {
+__device__ __forceinline__ void ghost_E(const R* Em, const BCEntry<R>& b, R* Ep) {
 #pragma unroll
   for (int c = 0; c < DIM * DIM; ++c) {
     int slot = DIM + 1 + c;
-    Ep[c] = ph.bc_mode[bc][slot] == 1 ? ph.bc_val[bc][slot] : Em[c];
+    Ep[c] = b.mode[slot] == 1 ? b.val[slot] : Em[c];
   }
 }
 
@@ -238,11 +249,11 @@ __device__ __forceinline__ void q_normal(R h, const R* E, const R* n, const Phys
 // ------------------------------------------------------------------ kernels
 
 template <int DIM, int P, typename R>
-__global__ void __launch_bounds__(128) estep_kernel(int K, const R* __restrict__ V, R* __restrict__ E,
+__global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__ V, R* __restrict__ E,
                                                     const R* __restrict__ geo, const int32_t* __restrict__ nbr,
                                                     const int8_t* __restrict__ nbrf, const R* __restrict__ fn,
                                                     const R* __restrict__ fsj, const EstepOps<DIM, P, R> ops,
-                                                    const Phys<R> ph) {
+                                                    const BCEntry<R>* __restrict__ bct) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NF = S::NF, NFP = S::NFP, NE = S::NE;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -298,7 +309,7 @@ __global__ void __launch_bounds__(128) estep_kernel(int K, const R* __restrict__
         for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (V[(1 + j) * KN + (size_t)e2 * NP + b] - u[j][a]);
       }
     } else {
-      const int bc = -1 - e2;
+      const BCEntry<R> bc = bct[-1 - e2];
 #pragma unroll
       for (int k = 0; k < NFP; ++k) {
         const int a = ops.fmask[f * NFP + k];
@@ -306,7 +317,7 @@ __global__ void __launch_bounds__(128) estep_kernel(int K, const R* __restrict__
         Vm[0] = R(1);
 #pragma unroll
         for (int j = 0; j < DIM; ++j) Vm[1 + j] = u[j][a];
-        ghost_V<DIM, R>(Vm, n, bc, ph, Vp);
+        ghost_V<DIM, R>(Vm, n, bc, Vp);
 #pragma unroll
         for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (Vp[1 + j] - Vm[1 + j]);
       }
@@ -329,13 +340,15 @@ __global__ void __launch_bounds__(128) estep_kernel(int K, const R* __restrict__
     for (int a = 0; a < NP; ++a) E[c * KN + (size_t)e * NP + a] = Eo[c][a];
 }
 
-template <int DIM, int P, typename R>
-__global__ void __launch_bounds__(128) face_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E,
+template <int DIM, int P, typename R, bool BATCH>
+__global__ void __launch_bounds__(256) face_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E,
                                                    const int32_t* __restrict__ fe1, const int8_t* __restrict__ ff1,
                                                    const int32_t* __restrict__ fe2, const int8_t* __restrict__ ff2,
                                                    const R* __restrict__ fnrm, const R* __restrict__ fsj,
                                                    R* __restrict__ wflux, const FaceOps<DIM, P, R> ops,
-                                                   const Phys<R> ph) {
+                                                   const Phys<R> ph0, const Phys<R>* __restrict__ ptab,
+                                                   const int32_t* __restrict__ inst,
+                                                   const BCEntry<R>* __restrict__ bct) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV, NE = S::NE;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -343,6 +356,7 @@ __global__ void __launch_bounds__(128) face_kernel(int K, int F, const R* __rest
   const int fc = t / NFQ, m = t - fc * NFQ;
   const size_t KN = (size_t)K * NP;
   const int e1 = fe1[fc], f1 = ff1[fc], e2 = fe2[fc];
+  const Phys<R> ph = BATCH ? ptab[inst[e1]] : ph0;
   R n[DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i) n[i] = fnrm[(size_t)i * F + fc];
@@ -376,8 +390,9 @@ __global__ void __launch_bounds__(128) face_kernel(int K, int F, const R* __rest
       for (int c = 0; c < NE; ++c) Ep[c] += L * E[c * KN + b];
     }
   } else {
-    ghost_V<DIM, R>(Vm, n, -1 - e2, ph, Vp);
-    ghost_E<DIM, R>(Em, -1 - e2, ph, Ep);
+    const BCEntry<R> bc = bct[-1 - e2];
+    ghost_V<DIM, R>(Vm, n, bc, Vp);
+    ghost_E<DIM, R>(Em, bc, Ep);
   }
   R Fn[NV], Qm[NV], Qp[NV];
   hll<DIM, R>(Vm, Vp, n, ph, Fn);
@@ -390,18 +405,21 @@ __global__ void __launch_bounds__(128) face_kernel(int K, int F, const R* __rest
 }
 
 // mode 0: write dV/dt to out; mode 1: out = c0 * V0 + c1 * (Vin + dt * dV/dt).
-template <int DIM, int P, typename R>
-__global__ void __launch_bounds__(128) volume_kernel(int K, int F, const R* __restrict__ Vin,
+template <int DIM, int P, typename R, bool BATCH>
+__global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __restrict__ Vin,
                                                      const R* V0, R* out,
                                                      const R* __restrict__ E, const R* __restrict__ bed,
                                                      const R* __restrict__ geo, const int32_t* __restrict__ fid,
                                                      const R* __restrict__ wflux, const VolOps<DIM, P, R> ops,
-                                                     const Phys<R> ph, int mode, R c0, R c1,
+                                                     const Phys<R> ph0, const Phys<R>* __restrict__ ptab,
+                                                     const int32_t* __restrict__ inst, int mode, R c0, R c1,
                                                      const DevScalars* __restrict__ sc) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NQ = S::NQ, NF = S::NF, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV, NE = S::NE;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= K) return;
+  const int ins = BATCH ? inst[e] : 0;
+  const Phys<R> ph = BATCH ? ptab[ins] : ph0;
   const size_t KN = (size_t)K * NP;
   const size_t eo = (size_t)e * NP;
   R G[2][2];
@@ -606,7 +624,7 @@ __global__ void __launch_bounds__(128) volume_kernel(int K, int F, const R* __re
 #pragma unroll
       for (int a = 0; a < NP; ++a) out[v * KN + eo + a] = dV[v][a];
   } else {
-    const R dt = (R)sc->dt;
+    const R dt = (R)sc[ins].dt;
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -677,7 +695,7 @@ __global__ void __launch_bounds__(256) dt_partial_kernel(int K, const R* __restr
 
 // Final step size: fixed dt (> 0) or min of the partials; advances t and the
 // step counter.  A negative partial latches DG_ERR_NONFINITE (4).
-__global__ void dt_finalize_kernel(int nblocks, const double* __restrict__ partial, double fixed_dt,
+static __global__ void dt_finalize_kernel(int nblocks, const double* __restrict__ partial, double fixed_dt,
                                    DevScalars* __restrict__ sc) {
   __shared__ double red[32];
   double v = 1e300;
@@ -728,7 +746,7 @@ __global__ void __launch_bounds__(256) mass_partial_kernel(int K, const R* __res
 }
 
 // Compensated (Kahan) sum of the block partials; which = 0 -> mass, 1 -> mass0 too.
-__global__ void mass_finalize_kernel(int nblocks, const double* __restrict__ partial, int set_ref,
+static __global__ void mass_finalize_kernel(int nblocks, const double* __restrict__ partial, int set_ref,
                                      DevScalars* __restrict__ sc) {
   if (threadIdx.x != 0) return;
   double s = 0.0, c = 0.0;
@@ -742,13 +760,179 @@ __global__ void mass_finalize_kernel(int nblocks, const double* __restrict__ par
   if (set_ref) sc->mass0 = s;
 }
 
+
+// ------------------------------------------------------------------ per-instance reductions (batches)
+
+// Stable step of a batch: each block takes one contiguous 256-element range
+// of one instance (blk_e[b] .. blk_e[b+1]) and writes its FP64 minimum to
+// partial[b]; a negative partial flags a non-finite state.
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(256) dt_block_kernel(int K, const int64_t* __restrict__ blk_e,
+                                                       const int32_t* __restrict__ blk_gid,
+                                                       const R* __restrict__ V, const R* __restrict__ geo,
+                                                       const double* __restrict__ iparm,
+                                                       double* __restrict__ partial) {
+  constexpr int NP = Sh<DIM, P>::NP;
+  __shared__ double red[8];
+  const int b = blockIdx.x;
+  const int g = blk_gid[b];
+  const int64_t e = blk_e[b] + threadIdx.x;
+  const double gc = iparm[4 * g + 0], h_floor = iparm[4 * g + 1], cfl = iparm[4 * g + 2], nu = iparm[4 * g + 3];
+  double dte = 1e300;
+  if (e < blk_e[b + 1]) {
+    const size_t KN = (size_t)K * NP;
+    double lam = 0.0;
+    bool bad = false;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      double h = (double)V[(size_t)e * NP + a];
+      double sp2 = 0.0;
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        double u = (double)V[(1 + j) * KN + (size_t)e * NP + a];
+        sp2 += u * u;
+      }
+      double l = sqrt(sp2) + sqrt(gc * fmax(h, h_floor));
+      if (!isfinite(l) || !isfinite(h)) bad = true;
+      lam = fmax(lam, l);
+    }
+    const double dx = (double)geo[5 * K + e];
+    const double qq = 2.0 * P + 1.0;
+    dte = cfl * dx / (qq * lam + qq * qq * 2.0 * nu / dx);
+    if (bad) dte = -1.0;
+  }
+  double v = warp_min(dte);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? red[lane] : 1e300;
+    v = warp_min(v);
+    if (lane == 0) partial[b] = v;
+  }
+}
+
+// One warp per instance of a group: minimum of its block partials (exact,
+// so independent of order), then dt, t, step count and dt_min/max.
+static __global__ void dt_members_kernel(int n_members, const int32_t* __restrict__ mblk,
+                                         const int32_t* __restrict__ gid, const double* __restrict__ partial,
+                                         DevScalars* __restrict__ sc) {
+  const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= n_members) return;
+  double m = 1e300;
+  for (int b = mblk[i] + lane; b < mblk[i + 1]; b += 32) m = fmin(m, partial[b]);
+  m = warp_min(m);
+  if (lane == 0) {
+    DevScalars& s = sc[gid[i]];
+    if (m < 0.0) {
+      s.status = 4;
+      m = 0.0;
+    }
+    s.dt = m;
+    s.t += m;
+    s.steps += 1;
+    s.dt_min = fmin(s.dt_min, m);
+    s.dt_max = fmax(s.dt_max, m);
+  }
+}
+
+// One block per instance: FP64 integral of h over the instance (fixed
+// reduction order, so repeated calls give identical sums).
+template <int NP, typename R>
+__global__ void __launch_bounds__(256) mass_instance_kernel(int K, const int64_t* __restrict__ ebeg,
+                                                            const int32_t* __restrict__ gid,
+                                                            const R* __restrict__ V, const R* __restrict__ geo,
+                                                            const double* __restrict__ wint, int set_ref,
+                                                            DevScalars* __restrict__ sc) {
+  __shared__ double red[8];
+  const int i = blockIdx.x;
+  const int64_t b = ebeg[i], en = ebeg[i + 1];
+  double acc = 0.0;
+  for (int64_t e = b + threadIdx.x; e < en; e += blockDim.x) {
+    double s = 0.0;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) s += wint[a] * (double)V[(size_t)e * NP + a];
+    acc += (double)geo[4 * K + e] * s;
+  }
+  double v = warp_sum(acc);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    DevScalars& s = sc[gid[i]];
+    s.mass = t;
+    if (set_ref) s.mass0 = t;
+  }
+}
+
+static __global__ void reset_scalars_array_kernel(int n, DevScalars* sc) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  sc[i].dt = 0.0;
+  sc[i].t = 0.0;
+  sc[i].dt_min = 1e300;
+  sc[i].dt_max = 0.0;
+  sc[i].steps = 0;
+  sc[i].status = 0;
+}
+
+// ------------------------------------------------------------------ host: operator tables
+
+template <int DIM, int P, typename R>
+void fill_ops(const RefOps& o, EstepOps<DIM, P, R>& eo, FaceOps<DIM, P, R>& fo, VolOps<DIM, P, R>& vo) {
+  using S = Sh<DIM, P>;
+  const int NP = S::NP, NQ = S::NQ;
+  for (int i = 0; i < NP * NP; ++i) {
+    eo.Dr[i] = (R)o.Dr[i];
+    eo.Ds[i] = (R)o.Ds[i];
+    vo.Minv[i] = (R)o.Minv[i];
+  }
+  for (int i = 0; i < NP * S::NF * S::NFP; ++i) eo.LIFT[i] = (R)o.LIFT[i];
+  for (int i = 0; i < S::NF * S::NFP; ++i) {
+    eo.fmask[i] = (int8_t)o.fmask[i];
+    fo.fmask[i] = (int8_t)o.fmask[i];
+    vo.fmask[i] = (int8_t)o.fmask[i];
+  }
+  for (int m = 0; m < S::NFQ; ++m) {
+    fo.wf[m] = (R)o.wf[m];
+    for (int k = 0; k < S::NFP; ++k) {
+      fo.Lf[m * S::NFP + k] = (R)o.Lf[m * S::NFP + k];
+      vo.LfT[k * S::NFQ + m] = (R)o.Lf[m * S::NFP + k];
+    }
+  }
+  for (int q = 0; q < NQ; ++q) {
+    vo.wq[q] = (R)o.wq[q];
+    for (int a = 0; a < NP; ++a) {
+      vo.Vq[q * NP + a] = (R)o.Vq[q * NP + a];
+      vo.Drq[q * NP + a] = (R)o.Drq[q * NP + a];
+      vo.Dsq[q * NP + a] = (R)o.Dsq[q * NP + a];
+      vo.Wr[q * NP + a] = (R)(o.wq[q] * o.Drq[q * NP + a]);
+      vo.Ws[q * NP + a] = (R)(o.wq[q] * o.Dsq[q * NP + a]);
+    }
+  }
+}
+
+// Maximum d sigma_B / dE over E (attained at E = 0) for the step bound.
+inline double max_bingham_slope(int reg, double sigma0, double gamma, double pap_m) {
+  if (!(sigma0 > 0.0)) return 0.0;
+  switch (reg) {
+    case 1: case 2: case 5: return 2.0 * gamma;
+    case 3: return 2.0 * sigma0 * gamma;
+    case 4: return 2.0 * sigma0 * pap_m;
+    default: return 0.0;
+  }
+}
+
 template <typename Rin, typename Rout>
 __global__ void convert_kernel(size_t n, const Rin* __restrict__ in, Rout* __restrict__ out) {
   size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = (Rout)in[i];
 }
 
-__global__ void reset_scalars_kernel(DevScalars* sc) {
+static __global__ void reset_scalars_kernel(DevScalars* sc) {
   sc->dt = 0.0;
   sc->t = 0.0;
   sc->dt_min = 1e300;

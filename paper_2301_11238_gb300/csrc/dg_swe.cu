@@ -8,7 +8,7 @@
 #include <vector>
 
 #include "../../include/dg_swe.h"
-#include "dg_host.h"
+#include "dg_ctx.h"
 #include "dg_kernels.cuh"
 
 using namespace dgswe;
@@ -21,35 +21,25 @@ constexpr int kGraphSteps = 16;
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-struct Driver;
-
 }  // namespace
 
-struct dg_swe_ctx {
-  int dim = 0, p = 0, reg = 0, prec = 0;
-  dg_swe_params prm{};
-  RefOps ops;
-  MeshData mesh;
-  std::vector<double> bed;
-  bool has_bed = false;
-  size_t rsize = 8;
-  // workspace
-  size_t ws_need = 0;
-  char* ws = nullptr;
-  struct {
-    size_t geo, nbr, nbrf, fid, fn, fsj, fe1, fe2, ff1, ff2, fnrm, fsjf, bed, V0, V1, V2, E, wflux, partial, wint, sc;
-  } off{};
-  int nblk_dt = 0, nblk_mass = 0;
-  cudaStream_t stream = nullptr;
-  cudaStream_t priv = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
-  cudaGraphExec_t g1 = nullptr, gN = nullptr;
-  std::unique_ptr<Driver> drv;
-  std::string err;
-
-  template <typename T>
-  T* at(size_t o) const { return reinterpret_cast<T*>(ws + o); }
+namespace dgswe {
+struct Driver {
+  virtual ~Driver() = default;
+  virtual void estep(dg_swe_ctx* c, const void* V, void* E, cudaStream_t s) = 0;
+  virtual void face(dg_swe_ctx* c, const void* V, const void* E, cudaStream_t s) = 0;
+  virtual void volume(dg_swe_ctx* c, const void* Vin, const void* V0, void* out, int mode, double c0,
+                      double c1, cudaStream_t s) = 0;
+  virtual void dt_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
+  virtual void mass_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
+  // Face flux and residual-mode volume pass with caller-chosen scratch for
+  // the face fluxes and E (used by dg_swe_residual_static).
+  virtual void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) = 0;
+  virtual void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
+                             cudaStream_t s) = 0;
 };
+void DriverDeleter::operator()(Driver* d) const { delete d; }
+}  // namespace dgswe
 
 namespace {
 
@@ -68,20 +58,7 @@ dg_status cuda_fail(dg_swe_ctx* c, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(c, e_, #call); \
   } while (0)
 
-struct Driver {
-  virtual ~Driver() = default;
-  virtual void estep(dg_swe_ctx* c, const void* V, void* E, cudaStream_t s) = 0;
-  virtual void face(dg_swe_ctx* c, const void* V, const void* E, cudaStream_t s) = 0;
-  virtual void volume(dg_swe_ctx* c, const void* Vin, const void* V0, void* out, int mode, double c0,
-                      double c1, cudaStream_t s) = 0;
-  virtual void dt_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
-  virtual void mass_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
-  // Face flux and residual-mode volume pass with caller-chosen scratch for
-  // the face fluxes and E (used by dg_swe_residual_static).
-  virtual void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) = 0;
-  virtual void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
-                             cudaStream_t s) = 0;
-};
+
 
 template <typename R>
 Phys<R> make_phys(const dg_swe_params& p, int reg) {
@@ -96,12 +73,18 @@ Phys<R> make_phys(const dg_swe_params& p, int reg) {
   ph.pap_m = (R)p.pap_m;
   ph.h_floor = (R)p.h_floor;
   ph.reg = reg;
-  for (int b = 0; b < DG_SWE_MAX_BC; ++b)
-    for (int s = 0; s < 7; ++s) {
-      ph.bc_mode[b][s] = b < p.n_bc ? p.bc[b].mode[s] : 0;
-      ph.bc_val[b][s] = (R)(b < p.n_bc ? p.bc[b].value[s] : 0.0);
-    }
   return ph;
+}
+
+template <typename R>
+std::vector<BCEntry<R>> make_bc_table(const dg_swe_params& p) {
+  std::vector<BCEntry<R>> t(p.n_bc);
+  for (int b = 0; b < p.n_bc; ++b)
+    for (int s = 0; s < 7; ++s) {
+      t[b].mode[s] = p.bc[b].mode[s];
+      t[b].val[s] = (R)p.bc[b].value[s];
+    }
+  return t;
 }
 
 template <int DIM, int P, typename R>
@@ -113,36 +96,7 @@ struct Impl final : Driver {
   Phys<R> ph{};
 
   explicit Impl(const dg_swe_ctx& c) {
-    const RefOps& o = c.ops;
-    const int NP = S::NP, NQ = S::NQ;
-    for (int i = 0; i < NP * NP; ++i) {
-      eo.Dr[i] = (R)o.Dr[i];
-      eo.Ds[i] = (R)o.Ds[i];
-      vo.Minv[i] = (R)o.Minv[i];
-    }
-    for (int i = 0; i < NP * S::NF * S::NFP; ++i) eo.LIFT[i] = (R)o.LIFT[i];
-    for (int i = 0; i < S::NF * S::NFP; ++i) {
-      eo.fmask[i] = (int8_t)o.fmask[i];
-      fo.fmask[i] = (int8_t)o.fmask[i];
-      vo.fmask[i] = (int8_t)o.fmask[i];
-    }
-    for (int m = 0; m < S::NFQ; ++m) {
-      fo.wf[m] = (R)o.wf[m];
-      for (int k = 0; k < S::NFP; ++k) {
-        fo.Lf[m * S::NFP + k] = (R)o.Lf[m * S::NFP + k];
-        vo.LfT[k * S::NFQ + m] = (R)o.Lf[m * S::NFP + k];
-      }
-    }
-    for (int q = 0; q < NQ; ++q) {
-      vo.wq[q] = (R)o.wq[q];
-      for (int a = 0; a < NP; ++a) {
-        vo.Vq[q * NP + a] = (R)o.Vq[q * NP + a];
-        vo.Drq[q * NP + a] = (R)o.Drq[q * NP + a];
-        vo.Dsq[q * NP + a] = (R)o.Dsq[q * NP + a];
-        vo.Wr[q * NP + a] = (R)(o.wq[q] * o.Drq[q * NP + a]);
-        vo.Ws[q * NP + a] = (R)(o.wq[q] * o.Dsq[q * NP + a]);
-      }
-    }
+    fill_ops<DIM, P, R>(c.ops, eo, fo, vo);
     ph = make_phys<R>(c.prm, c.reg);
   }
 
@@ -150,52 +104,44 @@ struct Impl final : Driver {
     const int K = (int)c->mesh.K;
     estep_kernel<DIM, P, R><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
         K, (const R*)V, (R*)E, c->at<R>(c->off.geo), c->at<int32_t>(c->off.nbr), c->at<int8_t>(c->off.nbrf),
-        c->at<R>(c->off.fn), c->at<R>(c->off.fsj), eo, ph);
+        c->at<R>(c->off.fn), c->at<R>(c->off.fsj), eo, c->at<BCEntry<R>>(c->off.bct));
   }
   void face(dg_swe_ctx* c, const void* V, const void* E, cudaStream_t s) override {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     const long long n = (long long)F * S::NFQ;
-    face_kernel<DIM, P, R><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+    face_kernel<DIM, P, R, false><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
         K, F, (const R*)V, (const R*)E, c->at<int32_t>(c->off.fe1), c->at<int8_t>(c->off.ff1),
         c->at<int32_t>(c->off.fe2), c->at<int8_t>(c->off.ff2), c->at<R>(c->off.fnrm), c->at<R>(c->off.fsjf),
-        c->at<R>(c->off.wflux), fo, ph);
+        c->at<R>(c->off.wflux), fo, ph, nullptr, nullptr, c->at<BCEntry<R>>(c->off.bct));
   }
   void volume(dg_swe_ctx* c, const void* Vin, const void* V0, void* out, int mode, double c0, double c1,
               cudaStream_t s) override {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
-    volume_kernel<DIM, P, R><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+    volume_kernel<DIM, P, R, false><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
         K, F, (const R*)Vin, (const R*)V0, (R*)out, c->at<R>(c->off.E),
         c->has_bed ? c->at<R>(c->off.bed) : nullptr, c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid),
-        c->at<R>(c->off.wflux), vo, ph, mode, (R)c0, (R)c1, c->at<DevScalars>(c->off.sc));
+        c->at<R>(c->off.wflux), vo, ph, nullptr, nullptr, mode, (R)c0, (R)c1, c->at<DevScalars>(c->off.sc));
   }
   void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) override {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     const long long n = (long long)F * S::NFQ;
-    face_kernel<DIM, P, R><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+    face_kernel<DIM, P, R, false><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
         K, F, (const R*)V, (const R*)E, c->at<int32_t>(c->off.fe1), c->at<int8_t>(c->off.ff1),
         c->at<int32_t>(c->off.fe2), c->at<int8_t>(c->off.ff2), c->at<R>(c->off.fnrm), c->at<R>(c->off.fsjf),
-        (R*)wflux, fo, ph);
+        (R*)wflux, fo, ph, nullptr, nullptr, c->at<BCEntry<R>>(c->off.bct));
   }
   void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
                      cudaStream_t s) override {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
-    volume_kernel<DIM, P, R><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+    volume_kernel<DIM, P, R, false><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
         K, F, (const R*)V, nullptr, (R*)out, (const R*)E, c->has_bed ? c->at<R>(c->off.bed) : nullptr,
-        c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid), (const R*)wflux, vo, ph, 0, R(0), R(0),
+        c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid), (const R*)wflux, vo, ph, nullptr, nullptr, 0, R(0), R(0),
         c->at<DevScalars>(c->off.sc));
   }
   void dt_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) override {
     const int K = (int)c->mesh.K;
-    double slope = 0.0;  // max d sigma_B / dE, attained at E = 0
     const auto& p = c->prm;
-    if (p.sigma0 > 0.0) {
-      switch (c->reg) {
-        case 1: case 2: case 5: slope = 2.0 * p.gamma; break;
-        case 3: slope = 2.0 * p.sigma0 * p.gamma; break;
-        case 4: slope = 2.0 * p.sigma0 * p.pap_m; break;
-        default: slope = 0.0;
-      }
-    }
+    const double slope = max_bingham_slope(c->reg, p.sigma0, p.gamma, p.pap_m);
     const double nu = (4.0 * p.eta + slope) / p.rho;
     dt_partial_kernel<DIM, P, R><<<c->nblk_dt, kRedBlock, 0, s>>>(
         K, (const R*)V, c->at<R>(c->off.geo), p.g * std::cos(p.alpha), p.h_floor, p.cfl, nu,
@@ -209,9 +155,9 @@ struct Impl final : Driver {
 };
 
 template <typename R>
-std::unique_ptr<Driver> make_driver(const dg_swe_ctx& c) {
+DriverPtr make_driver(const dg_swe_ctx& c) {
 #define DG_CASE(D, P) \
-  if (c.dim == D && c.p == P) return std::unique_ptr<Driver>(new Impl<D, P, R>(c));
+  if (c.dim == D && c.p == P) return DriverPtr(new Impl<D, P, R>(c));
   DG_CASE(1, 1) DG_CASE(1, 2) DG_CASE(1, 3) DG_CASE(2, 1) DG_CASE(2, 2) DG_CASE(2, 3)
 #undef DG_CASE
   return nullptr;
@@ -388,6 +334,7 @@ dg_status dg_swe_init(const dg_swe_mesh* mesh, int order, int regularization, co
   c->off.partial = take((size_t)c->nblk_dt * 8);
   c->off.wint = take((size_t)Np * 8);
   c->off.sc = take(sizeof(DevScalars));
+  c->off.bct = take((size_t)p.n_bc * (c->rsize == 8 ? sizeof(BCEntry<double>) : sizeof(BCEntry<float>)));
   c->ws_need = o;
   *out = c.release();
   return DG_OK;
@@ -434,6 +381,15 @@ dg_status dg_swe_set_workspace(dg_swe_ctx* c, void* ptr, size_t bytes) {
   CK(up_real(c->off.fsjf, m.face_sj));
   if (c->has_bed) CK(up_real(c->off.bed, c->bed));
   CK(cudaMemcpyAsync(c->ws + c->off.wint, c->ops.wint.data(), c->ops.Np * 8, cudaMemcpyHostToDevice, s));
+  if (c->rsize == 8) {
+    auto t = make_bc_table<double>(c->prm);
+    CK(cudaMemcpyAsync(c->ws + c->off.bct, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  } else {
+    auto t = make_bc_table<float>(c->prm);
+    CK(cudaMemcpyAsync(c->ws + c->off.bct, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
   CK(cudaMemsetAsync(c->ws + c->off.E, 0, (size_t)c->dim * c->dim * K * c->ops.Np * c->rsize, s));
   reset_scalars_kernel<<<1, 1, 0, s>>>(c->at<DevScalars>(c->off.sc));
   CK(cudaGetLastError());

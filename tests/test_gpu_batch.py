@@ -1,0 +1,93 @@
+"""Batched ensembles on the GPU: every batched instance must evolve exactly
+as the same instance run alone (FP64, bitwise), and, transitively, as the
+oracle; the autotuner must not change results."""
+import numpy as np
+import pytest
+
+import synth
+from helpers import rel_l2, smooth_case
+from oracle.run import build as oracle_build, run_explicit
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _mixed_cases():
+    a = synth.dam_break_1d(n_el=70, order=1)
+    b = synth.radial_dam_2d(n=10, order=2, reg=1, sigma0=0.02)
+    c = synth.radial_dam_2d(n=7, order=2, reg=3, sigma0=0.1, gamma=50.0)
+    d = smooth_case(1, 3, 2, n=40, seed=5, bc="dirichlet")
+    e = smooth_case(2, 1, 5, n=6, seed=6, bc="wall")
+    f = synth.bump_dam_2d(n=6, order=3)
+    return [a, b, c, d, e, f]
+
+
+def test_batch_matches_single_instances_bitwise():
+    import paper_2301_11238_gb300 as G
+    cases = _mixed_cases()
+    B, V0s = G.batch_from_cases(cases)
+    stB = B.run(25)
+    for i, c in enumerate(cases):
+        s, V0, _ = G.solver_from_case(c)
+        st = s.run(25)
+        V = s.get_state(with_E=False)
+        VB = B.get_state(i)
+        assert np.array_equal(V, VB), (i, rel_l2(VB, V))
+        assert stB[i]["t"] == st["t"] and stB[i]["steps"] == 25
+        assert abs(stB[i]["mass"] - st["mass"]) <= 1e-14 * abs(st["mass"])
+        s.close()
+    B.close()
+
+
+def test_batch_instance_matches_oracle():
+    import paper_2301_11238_gb300 as G
+    c = synth.radial_dam_2d(n=8, order=2, reg=2, sigma0=0.1)
+    other = synth.dam_break_1d(n_el=50, order=2)
+    B, _ = G.batch_from_cases([other, c])
+    d, V0, _ = oracle_build(c)
+    Vo, _, t = run_explicit(d, V0, 20)
+    st = B.run(20)
+    assert abs(st[1]["t"] - t) < 1e-12 * t
+    assert rel_l2(B.get_state(1), Vo) < 1e-12
+
+
+def test_autotune_keeps_results():
+    import paper_2301_11238_gb300 as G
+    cases = _mixed_cases()[:3]
+    B1, _ = G.batch_from_cases(cases)
+    B2, _ = G.batch_from_cases(cases)
+    tiles = B2.autotune(3)
+    assert all(t in (32, 64, 128, 256) for g in tiles for t in g)
+    B1.run(10)
+    B2.run(10)
+    for i in range(len(cases)):
+        assert np.array_equal(B1.get_state(i), B2.get_state(i))
+
+
+def test_batch_fp32_close_to_fp64():
+    import paper_2301_11238_gb300 as G
+    cases = _mixed_cases()[:3]
+    B64, _ = G.batch_from_cases(cases)
+    B32, _ = G.batch_from_cases(cases, precision=G.PREC_FP32)
+    B64.run(20)
+    B32.run(20)
+    for i in range(3):
+        assert rel_l2(B32.get_state(i), B64.get_state(i)) < 1e-5
+
+
+def test_batch_nonfinite_names_instance():
+    import paper_2301_11238_gb300 as G
+    cases = _mixed_cases()[:2]
+    B, V0s = G.batch_from_cases(cases)
+    V = V0s[1].copy()
+    V[0, 5, 0] = np.inf
+    B.set_state(1, V)
+    with pytest.raises(G.DGError) as ei:
+        B.run(2)
+    assert ei.value.status == G.DG_ERR_NONFINITE and "instance 1" in str(ei.value)
