@@ -77,7 +77,8 @@ def dphi(s, prm):
         return np.where(x >= s0 + e, 0.0,
                         np.where(x <= s0 - e, 2.0 * g, 2.0 * b * g * (s0 - x + e)))
     if reg == 3:
-        return 2.0 * s0 * g / np.cosh(g * s) ** 2
+        x = np.minimum(g * s, 350.0)  # sech^2 underflows to 0 long before cosh overflows
+        return 2.0 * s0 * g / np.cosh(x) ** 2
     if reg == 4:
         return 2.0 * s0 * m * np.exp(-m * s)
     if reg == 5:
