@@ -54,7 +54,7 @@ def phi(s, prm):
     if reg == 3:
         return 2.0 * s0 * np.tanh(g * s)
     if reg == 4:
-        return 2.0 * s0 * (1.0 - np.exp(-m * s))
+        return -2.0 * s0 * np.expm1(-m * s)  # 2 sigma0 (1 - exp(-m s)), without cancellation at small s
     if reg == 5:
         return np.minimum(2.0 * g * s, 2.0 * s0)
     raise ValueError(reg)
