@@ -365,3 +365,104 @@ def batch_from_cases(cases, precision=PREC_FP64, stream=None):
     for i, V0 in enumerate(V0s):
         b.set_state(i, V0)
     return b, V0s
+
+
+class Implicit:
+    """Backward Euler + Newton, 1D (include/dg_implicit.h)."""
+
+    def __init__(self, coords, etov, order, reg, prm, dt, m3=-1, face_bc=None, bcs=None, bed=None,
+                 max_it=10, on_fail_continue=True, rtol=1e-10, atol=1e-13, xtol=1e-14, device="cuda",
+                 stream=None, allocate=True):
+        self.L = _lib.lib()
+        self.order = int(order)
+        self._coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1, 1)
+        self._etov = np.ascontiguousarray(etov, dtype=np.int32)
+        self._face_bc = None if face_bc is None else np.ascontiguousarray(face_bc, dtype=np.int8)
+        self._bed = None if bed is None else np.ascontiguousarray(bed, dtype=np.float64)
+        m = _lib.Mesh()
+        m.dim = 1
+        m.n_vertices = self._coords.shape[0]
+        m.coords = self._coords.ctypes.data
+        m.n_elements = self._etov.shape[0]
+        m.elem_vertices = self._etov.ctypes.data
+        m.face_bc = None if self._face_bc is None else self._face_bc.ctypes.data
+        m.bed = None if self._bed is None else self._bed.ctypes.data
+        self._params = make_params(prm, bcs, PREC_FP64)
+        ip = _lib.ImplicitParams(dt=float(dt), m3=int(m3), max_it=int(max_it),
+                                 on_fail_continue=1 if on_fail_continue else 0, rtol=rtol, atol=atol, xtol=xtol)
+        ctx = C.c_void_p()
+        st = self.L.dg_implicit_init(C.byref(m), self.order, int(reg), C.byref(self._params), C.byref(ip),
+                                     C.byref(ctx))
+        self.ctx = ctx
+        if st != DG_OK:
+            msg = self.L.dg_implicit_last_error(ctx).decode() if ctx.value else ""
+            if ctx.value:
+                self.L.dg_implicit_destroy(ctx)
+                self.ctx = C.c_void_p()
+            raise DGError(st, msg)
+        self.K = self._etov.shape[0]
+        self.Np = self.order + 1
+        self.NpE = (self.order if m3 < 0 else int(m3)) + 1
+        self.workspace = None
+        if allocate:
+            torch = _torch()
+            nbytes = int(self.L.dg_implicit_workspace_size(self.ctx))
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.workspace.device)
+            self._check(self.L.dg_implicit_set_stream(self.ctx, C.c_void_p(self.stream.cuda_stream)))
+            self._check(self.L.dg_implicit_set_workspace(self.ctx, C.c_void_p(self.workspace.data_ptr()), nbytes))
+
+    def _check(self, st):
+        if st != DG_OK:
+            raise DGError(st, self.L.dg_implicit_last_error(self.ctx).decode())
+
+    def node_coords(self):
+        out = np.empty((self.K, self.Np, 1))
+        self._check(self.L.dg_implicit_node_coords(self.ctx, out.ctypes.data))
+        return out
+
+    def set_state(self, V):
+        V = np.ascontiguousarray(V, dtype=np.float64)
+        assert V.shape == (2, self.K, self.Np)
+        self._check(self.L.dg_implicit_set_state(self.ctx, V.ctypes.data, 0))
+
+    def get_state(self):
+        V = np.empty((2, self.K, self.Np))
+        E = np.empty((self.K, self.NpE))
+        self._check(self.L.dg_implicit_get_state(self.ctx, V.ctypes.data, E.ctypes.data, 0))
+        return V, E
+
+    def run(self, n_steps):
+        st = _lib.ImplicitStats()
+        self._check(self.L.dg_implicit_run(self.ctx, int(n_steps), C.byref(st)))
+        return dict(steps=st.steps, newton_its=st.newton_its, failed_steps=st.failed_steps, t=st.t,
+                    last_its=st.last_its, status=st.status)
+
+    def active_percent(self):
+        v = C.c_double()
+        self._check(self.L.dg_implicit_active_percent(self.ctx, C.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "ctx", None) is not None and self.ctx.value:
+            self.L.dg_implicit_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def implicit_from_case(case, dt=None, **kw):
+    """Implicit integrator for a 1D synthetic case with its state set."""
+    probe = Implicit(case.coords, case.etov, case.order, case.params["reg"], case.params, dt or case.dt or 1e-3,
+                     m3=case.m3, face_bc=case.face_bc, bcs=case.bcs, allocate=False)
+    V0, bed = case.initial_state(probe.node_coords())
+    probe.close()
+    s = Implicit(case.coords, case.etov, case.order, case.params["reg"], case.params, dt or case.dt,
+                 m3=case.m3, face_bc=case.face_bc, bcs=case.bcs,
+                 bed=bed if case.bed_fn is not None else None, **kw)
+    s.set_state(V0)
+    return s, V0

@@ -34,14 +34,15 @@ class Stats(C.Structure):
 
 
 class ImplicitParams(C.Structure):
-    _fields_ = [("dt", C.c_double), ("max_it", C.c_int32), ("on_fail_continue", C.c_int32),
-                ("rtol", C.c_double), ("atol", C.c_double), ("m3", C.c_int32),
-                ("n_gamma", C.c_int32), ("gamma0", C.c_double)]
+    _fields_ = [("dt", C.c_double), ("m3", C.c_int32), ("max_it", C.c_int32),
+                ("on_fail_continue", C.c_int32), ("rtol", C.c_double), ("atol", C.c_double),
+                ("xtol", C.c_double)]
 
 
 class ImplicitStats(C.Structure):
     _fields_ = [("steps", C.c_int64), ("newton_its", C.c_int64), ("failed_steps", C.c_int64),
-                ("t", C.c_double), ("last_res", C.c_double), ("status", C.c_int32)]
+                ("t", C.c_double), ("last_res", C.c_double), ("last_its", C.c_int32),
+                ("status", C.c_int32)]
 
 
 _SIGS = {
@@ -68,12 +69,18 @@ _SIGS = {
 }
 
 _OPTIONAL_SIGS = {
-    "dg_swe_implicit_step": (C.c_int, [C.c_void_p, C.POINTER(ImplicitParams), C.POINTER(ImplicitStats)]),
-    "dg_swe_implicit_run": (C.c_int, [C.c_void_p, C.POINTER(ImplicitParams), C.c_int64,
-                                      C.POINTER(ImplicitStats)]),
-    "dg_swe_implicit_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double,
-                                           C.c_int, C.c_void_p, C.c_void_p]),
-    "dg_swe_implicit_get_E": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dg_implicit_init": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.POINTER(ImplicitParams),
+                                   C.POINTER(C.c_void_p)]),
+    "dg_implicit_workspace_size": (C.c_size_t, [C.c_void_p]),
+    "dg_implicit_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "dg_implicit_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dg_implicit_node_coords": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "dg_implicit_set_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "dg_implicit_get_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int]),
+    "dg_implicit_run": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(ImplicitStats)]),
+    "dg_implicit_active_percent": (C.c_int, [C.c_void_p, C.POINTER(C.c_double)]),
+    "dg_implicit_last_error": (C.c_char_p, [C.c_void_p]),
+    "dg_implicit_destroy": (None, [C.c_void_p]),
     "dg_batch_init": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                 C.c_void_p, C.POINTER(C.c_void_p)]),
     "dg_batch_workspace_size": (C.c_size_t, [C.c_void_p]),
