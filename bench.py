@@ -39,17 +39,39 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="radial",
+                    choices=["radial", "dam1d", "bump", "ensemble", "slump"],
+                    help="radial: 9-instance radial dam-break sweep (64x64x2, p=2); dam1d: 1D dam break "
+                         "(200 el, p=1); bump: dam break over a bump (512x512x2 jittered, p=3); ensemble: "
+                         "256 heterogeneous instances; slump: 2048x2048x2 Bingham slump (p=2)")
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
     ap.add_argument("--mode", default="batch", choices=["batch", "solo"],
                     help="batch: all instances in one dg_batch (one launch per phase); solo: one context each")
-    ap.add_argument("--inner", type=int, default=100, help="RK3 steps per instance per bench step")
-    ap.add_argument("--n", type=int, default=64, help="squares per side of the triangulation")
+    ap.add_argument("--inner", type=int, default=None, help="RK3 steps per instance per bench step")
+    ap.add_argument("--n", type=int, default=None, help="squares per side (radial workload)")
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
-    return ap.parse_args()
+    a = ap.parse_args()
+    d = WORKLOAD_DEFAULTS[a.workload]
+    if a.precision is None:
+        a.precision = d["precision"]
+    if a.inner is None:
+        a.inner = d["inner"]
+    if a.n is None:
+        a.n = 64
+    return a
+
+
+WORKLOAD_DEFAULTS = {
+    "radial": dict(precision="fp64", inner=100),
+    "dam1d": dict(precision="fp64", inner=100),
+    "bump": dict(precision="fp32", inner=10),
+    "ensemble": dict(precision="fp32", inner=10),
+    "slump": dict(precision="fp32", inner=5),
+}
 
 
 def sweep_cases(n, order):
@@ -62,9 +84,45 @@ def sweep_cases(n, order):
     return out
 
 
+def workload_cases(args):
+    import synth
+    if args.workload == "radial":
+        return sweep_cases(args.n, args.order)
+    if args.workload == "dam1d":
+        return [synth.dam_break_1d()]
+    if args.workload == "bump":
+        return [synth.bump_dam_2d()]
+    if args.workload == "ensemble":
+        return synth.ensemble_cases()
+    return [synth.slump_2d()]
+
+
+def sample_case(workload, n, order):
+    """The bounded sample the CPU oracle times (and the accuracy check runs):
+    the workload itself when it is small, else the same physics on a smaller
+    mesh (stated in the JSON line)."""
+    import synth
+    if workload == "radial":
+        return sweep_cases(n, order)[0], f"instance 0 (sigma0=0, reg 1) of the sweep, {n}x{n}x2, full size"
+    if workload == "dam1d":
+        return synth.dam_break_1d(), "the full 1D dam break (200 elements, p=1)"
+    if workload == "bump":
+        return synth.bump_dam_2d(n=32), "bump dam break on a 32x32x2 jittered mesh (p=3), same physics"
+    if workload == "ensemble":
+        c = synth.ensemble_cases(n_inst=8, size_scale=0.1)[1]
+        return c, f"one ensemble-style instance ({c.dim}D, p={c.order}, {c.etov.shape[0]} elements)"
+    return synth.slump_2d(n=32), "Bingham slump on a 32x32x2 mesh (p=2), same physics"
+
+
 def workload_name(args):
-    return (f"radial_dam_2d {args.n}x{args.n}x2 triangles on [-1,1]^2, p={args.order}, "
-            f"sigma0 in {list(SIGMAS)} x regularization in {list(REGS)} (gamma=beta=1e3, eta=0.01)")
+    if args.workload == "radial":
+        return (f"radial_dam_2d {args.n}x{args.n}x2 triangles on [-1,1]^2, p={args.order}, "
+                f"sigma0 in {list(SIGMAS)} x regularization in {list(REGS)} (gamma=beta=1e3, eta=0.01)")
+    return {"dam1d": "dam_break_1d 200 elements on [0,1], p=1, exponential regularization m=1e3, sigma0=0.05",
+            "bump": "bump_dam_2d 512x512x2 jittered triangles (seed 3), p=3, tanh regularization gamma=1e3",
+            "ensemble": "ensemble of 256 instances (seed 4): 1D/2D, p in {1,2,3}, 1e3..5e4 elements",
+            "slump": "slump_2d 2048x2048x2 triangles, p=2, slope 0.05, 16-mode bed (seed 5), bi-viscosity"}[
+        args.workload]
 
 
 # ---------------------------------------------------------------- analytic counts
@@ -219,8 +277,7 @@ def oracle_worker(spec_path):
     with open(spec_path) as f:
         spec = json.load(f)
     from oracle.run import build as oracle_build
-    cases = sweep_cases(spec["n"], spec["order"])
-    case = cases[spec.get("instance", 0)]
+    case, _ = sample_case(spec["workload"], spec["n"], spec["order"])
     d, V0, _ = oracle_build(case)
     Vh = d.to_modal(V0)
     units = d.K * d.Np * d.nV
@@ -241,9 +298,10 @@ def oracle_worker(spec_path):
         json.dump(out, f)
 
 
-def run_oracle_subprocess(n, order, seconds, min_steps=1, max_steps=10 ** 9, return_state=False):
+def run_oracle_subprocess(workload, n, order, seconds, min_steps=1, max_steps=10 ** 9, return_state=False):
     with tempfile.TemporaryDirectory() as td:
-        spec = dict(n=n, order=order, seconds=seconds, min_steps=min_steps, max_steps=max_steps,
+        spec = dict(workload=workload, n=n, order=order, seconds=seconds, min_steps=min_steps,
+                    max_steps=max_steps,
                     out=os.path.join(td, "out.json"), return_state=return_state)
         sp = os.path.join(td, "spec.json")
         with open(sp, "w") as f:
@@ -262,8 +320,9 @@ def reference_main(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    res = run_oracle_subprocess(args.n, args.order, seconds=0.0, min_steps=args.warmup + args.steps,
-                                max_steps=args.warmup + args.steps)
+    res = run_oracle_subprocess(args.workload, args.n, args.order, seconds=0.0,
+                                min_steps=args.warmup + args.steps, max_steps=args.warmup + args.steps)
+    _, sample_desc = sample_case(args.workload, args.n, args.order)
     times = res["step_times"][args.warmup:]
     secs = sum(times)
     value = res["units_per_step"] * len(times) / secs
@@ -271,9 +330,9 @@ def reference_main(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": workload_name(args), "sample": "one SSP-RK3 step of instance 0 per step"},
+            "config": {"workload": workload_name(args), "sample": f"one SSP-RK3 step per step of {sample_desc}"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{len(times)} SSP-RK3 steps of instance 0 (sigma0=0, reg 1)"},
+                             "sample": f"{len(times)} SSP-RK3 steps of {sample_desc}"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -301,7 +360,7 @@ def main():
         dist.init_process_group("nccl")
     prec = G.PREC_FP64 if args.precision == "fp64" else G.PREC_FP32
     stream = torch.cuda.Stream()
-    cases = sweep_cases(args.n, args.order)
+    cases = workload_cases(args)
     batch, solvers, V0s, tiles = None, [], [], None
     with torch.cuda.stream(stream):
         if args.mode == "batch":
@@ -358,12 +417,21 @@ def main():
     # ---- dominant kernel: live per-launch timing on the launching stream
     with torch.cuda.stream(stream):
         if batch is not None:
-            kt = batch.time_kernels(20)[0]
-            K = batch.info()["elements"]
+            groups = []
+            for c in cases:
+                key = (c.dim, c.order)
+                if key not in [g[0] for g in groups]:
+                    groups.append([key, 0])
+                for g in groups:
+                    if g[0] == key:
+                        g[1] += c.etov.shape[0]
+            kts = batch.time_kernels(10)
+            gi = max(range(len(kts)), key=lambda i: kts[i]["volume"])
+            kt = kts[gi]
+            (dim, p), K = groups[gi]
         else:
-            kt = solvers[3].time_kernels(20)  # instance 3: sigma0 = 0.02, regularization 1
-            K = solvers[3].K
-    dim, p = 2, args.order
+            kt = solvers[min(3, len(solvers) - 1)].time_kernels(20)
+            dim, p, K = cases[0].dim, cases[0].order, solvers[min(3, len(solvers) - 1)].K
     vol_ms = kt["volume"]
     flops = volume_flops(dim, p) * K
     rs = 8 if prec == G.PREC_FP64 else 4
@@ -371,8 +439,8 @@ def main():
     achieved_tf = flops / (vol_ms * 1e-3) / 1e12
     pk, pk_kind = peaks()
     vbytes = volume_bytes(dim, p, rs) * K
-    wl_key = f"{args.mode}_{args.precision}_n{args.n}_p{args.order}"
-    roof = {"bound": "alu", "kernel": f"volume_kernel<2,{p},{'double' if rs == 8 else 'float'},"
+    wl_key = f"{args.workload}_{args.mode}_{args.precision}"
+    roof = {"bound": "alu", "kernel": f"volume_kernel<{dim},{p},{'double' if rs == 8 else 'float'},"
                                       f"{'true' if batch is not None else 'false'}>",
             "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
             "peak_source": ("FP64 pipe: 152 SMs x 2070 MHz x 2 flop x 2 DFMA/clk/SM = 1.26 TFLOP/s "
@@ -429,33 +497,31 @@ def main():
     cpu = None
     acc = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        res = run_oracle_subprocess(args.n, args.order, seconds=args.oracle_seconds, min_steps=2,
+        res = run_oracle_subprocess(args.workload, args.n, args.order, seconds=args.oracle_seconds, min_steps=2,
                                     return_state=True)
+        sc, sdesc = sample_case(args.workload, args.n, args.order)
         cpu = {"value": res["units_per_step"] * res["steps"] / res["seconds"], "unit": UNIT, "cores": 1,
                "kind": "oracle",
-               "sample": f"{res['steps']} SSP-RK3 steps of instance 0 (sigma0=0, reg 1), "
-                         f"{res['seconds']:.1f} s on one host core"}
+               "sample": f"{res['steps']} SSP-RK3 steps of {sdesc}, {res['seconds']:.1f} s on one host core"}
         with torch.cuda.stream(stream):
-            if batch is not None:
-                batch.set_state(0, V0s[0])
-                batch.run(res["steps"])
-                Vg = batch.get_state(0)
-            else:
-                solvers[0].set_state(V0s[0])
-                solvers[0].run(res["steps"])
-                Vg = solvers[0].get_state(with_E=False)
+            s_acc, _, _ = G.solver_from_case(sc, precision=prec, stream=stream)
+            s_acc.run(res["steps"])
+            Vg = s_acc.get_state(with_E=False)
+            s_acc.close()
         Vo = np.asarray(res["final"])
         acc = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
-               "after_steps": res["steps"], "instance": "sigma0=0, reg 1"}
+               "after_steps": res["steps"], "case": sdesc, "precision": args.precision}
 
-    dt_info = {f"sigma0={c.params['sigma0']},reg={c.params['reg']}": st["dt_last"]
-               for c, st in zip(cases, stats)}
+    dt_info = ({f"sigma0={c.params['sigma0']},reg={c.params['reg']}": st["dt_last"]
+                for c, st in zip(cases, stats)} if len(cases) <= 16 else
+               {"min": min(st["dt_last"] for st in stats), "max": max(st["dt_last"] for st in stats)})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64" if rs == 8 else "f32",
             "data": "synthetic",
-            "config": {"workload": workload_name(args), "instances": len(V0s), "elements_total": K
-                       if batch is not None else K * len(V0s), "mode": args.mode, "tiles": tiles,
+            "config": {"workload": workload_name(args), "instances": len(V0s),
+                       "elements_total": int(sum(c.etov.shape[0] for c in cases)), "mode": args.mode,
+                       "tiles": tiles,
                        "inner_rk3_steps_per_step": args.inner, "l2": "flushed (256 MiB write) before each step",
                        "parallelism": f"replicas x{world}", "dt_last": dt_info},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,

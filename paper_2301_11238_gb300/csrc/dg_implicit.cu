@@ -32,7 +32,7 @@ struct ImplOps {
 
 struct ImplArgs {
   int K;
-  double dt, gc, gs, rho_inv, eta, sigma0, gamma, beta, pap_m, h_floor;
+  double dt, inv_dt, gc, gs, rho_inv, eta, sigma0, gamma, beta, pap_m, h_floor;
   int reg;
   double rtol, atol, xtol;
   int max_it, on_fail_continue;
@@ -257,13 +257,13 @@ __device__ double assemble(int e, const ImplArgs& a, const ImplOps<P, M3>& o) {
 #pragma unroll
     for (int q = 0; q < NQ; ++q) {
       const double w = o.wq[q], l = o.Vq[q * NP + i], dl = o.dVq[q * NP + i];
-      rh += w * J * l * qh[q] / a.dt - w * dl * qh[q] * qu[q];
-      ru += w * J * l * qh[q] * qu[q] / a.dt
+      rh += w * J * l * qh[q] * a.inv_dt - w * dl * qh[q] * qu[q];
+      ru += w * J * l * qh[q] * qu[q] * a.inv_dt
             + w * dl * (qh[q] * qs[q] * a.rho_inv - (qh[q] * qu[q] * qu[q] + 0.5 * a.gc * qh[q] * qh[q]))
             + w * J * l * (a.gs * qh[q] + a.gc * qh[q] * qdH[q]);
     }
-    rh -= uo[i] / a.dt;
-    ru -= uo[NP + i] / a.dt;
+    rh -= uo[i] * a.inv_dt;
+    ru -= uo[NP + i] * a.inv_dt;
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
       rh += o.lf[f * NP + i] * Fh[f];
@@ -308,12 +308,12 @@ __device__ double assemble(int e, const ImplArgs& a, const ImplOps<P, M3>& o) {
         const double dlr = rb < 2 ? o.dVq[q * NP + ri] : o.dVEq[q * NE + ri];
         const double lc = cb < 2 ? o.Vq[q * NP + ci] : o.VEq[q * NE + ci];
         const double hq = qh[q], uq = qu[q];
-        if (rb == 0 && cb == 0) dv += w * J * lr * lc / a.dt - w * dlr * uq * lc;
+        if (rb == 0 && cb == 0) dv += w * J * lr * lc * a.inv_dt - w * dlr * uq * lc;
         else if (rb == 0 && cb == 1) dv += -w * dlr * hq * lc;
         else if (rb == 1 && cb == 0)
-          dv += w * J * lr * uq * lc / a.dt - w * dlr * (uq * uq + a.gc * hq) * lc + w * dlr * qs[q] * a.rho_inv * lc
+          dv += w * J * lr * uq * lc * a.inv_dt - w * dlr * (uq * uq + a.gc * hq) * lc + w * dlr * qs[q] * a.rho_inv * lc
                 + w * J * lr * (a.gs + a.gc * qdH[q]) * lc;
-        else if (rb == 1 && cb == 1) dv += w * J * lr * hq * lc / a.dt - w * dlr * 2.0 * hq * uq * lc;
+        else if (rb == 1 && cb == 1) dv += w * J * lr * hq * lc * a.inv_dt - w * dlr * 2.0 * hq * uq * lc;
         else if (rb == 1 && cb == 2) dv += w * dlr * hq * qds[q] * a.rho_inv * lc;
         else if (rb == 2 && cb == 2) dv += w * J * lr * lc;
         else if (rb == 2 && cb == 1) dv += w * dlr * lc;
@@ -654,6 +654,7 @@ ImplArgs make_args(dg_implicit* s) {
   const auto& p = s->prm;
   a.K = (int)s->K;
   a.dt = s->ip.dt;
+  a.inv_dt = 1.0 / s->ip.dt;
   a.gc = p.g * std::cos(p.alpha);
   a.gs = p.g * std::sin(p.alpha);
   a.rho_inv = 1.0 / p.rho;

@@ -662,24 +662,25 @@ __global__ void __launch_bounds__(256) dt_partial_kernel(int K, const R* __restr
   double dte = 1e300;
   if (e < K) {
     const size_t KN = (size_t)K * NP;
-    double lam = 0.0;
+    // wave speeds in the state's precision, step and reduction in FP64
+    R lam = R(0);
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
-      double h = (double)V[(size_t)e * NP + a];
-      double sp2 = 0.0;
+      const R h = V[(size_t)e * NP + a];
+      R sp2 = R(0);
 #pragma unroll
       for (int j = 0; j < DIM; ++j) {
-        double u = (double)V[(1 + j) * KN + (size_t)e * NP + a];
+        const R u = V[(1 + j) * KN + (size_t)e * NP + a];
         sp2 += u * u;
       }
-      double l = sqrt(sp2) + sqrt(gc * fmax(h, h_floor));
-      if (!(l == l) || !isfinite(l) || !isfinite(h)) bad = true;
+      const R l = sqrt(sp2) + sqrt((R)gc * fmax(h, (R)h_floor));
+      if (!isfinite(l) || !isfinite(h)) bad = true;
       lam = fmax(lam, l);
     }
     const double dx = (double)geo[5 * K + e];
     const double qq = 2.0 * P + 1.0;
-    dte = cfl * dx / (qq * lam + qq * qq * 2.0 * nu / dx);
+    dte = cfl * dx / (qq * (double)lam + qq * qq * 2.0 * nu / dx);
     if (bad) dte = -1.0;
   }
   double v = warp_min(dte);
@@ -781,24 +782,24 @@ __global__ void __launch_bounds__(256) dt_block_kernel(int K, const int64_t* __r
   double dte = 1e300;
   if (e < blk_e[b + 1]) {
     const size_t KN = (size_t)K * NP;
-    double lam = 0.0;
+    R lam = R(0);
     bool bad = false;
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
-      double h = (double)V[(size_t)e * NP + a];
-      double sp2 = 0.0;
+      const R h = V[(size_t)e * NP + a];
+      R sp2 = R(0);
 #pragma unroll
       for (int j = 0; j < DIM; ++j) {
-        double u = (double)V[(1 + j) * KN + (size_t)e * NP + a];
+        const R u = V[(1 + j) * KN + (size_t)e * NP + a];
         sp2 += u * u;
       }
-      double l = sqrt(sp2) + sqrt(gc * fmax(h, h_floor));
+      const R l = sqrt(sp2) + sqrt((R)gc * fmax(h, (R)h_floor));
       if (!isfinite(l) || !isfinite(h)) bad = true;
       lam = fmax(lam, l);
     }
     const double dx = (double)geo[5 * K + e];
     const double qq = 2.0 * P + 1.0;
-    dte = cfl * dx / (qq * lam + qq * qq * 2.0 * nu / dx);
+    dte = cfl * dx / (qq * (double)lam + qq * qq * 2.0 * nu / dx);
     if (bad) dte = -1.0;
   }
   double v = warp_min(dte);
