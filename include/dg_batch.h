@@ -57,7 +57,9 @@ dg_status dg_batch_stats(dg_batch *b, dg_swe_stats *stats);
 
 /* Autotuner: for every group and each of the three stage kernels, times
  * thread-block sizes {32, 64, 128, 256} on the current state (n_iter
- * launches each, CUDA events) and keeps the fastest.  Synchronizes; the step
+ * launches each, CUDA events) and keeps the fastest.  The face kernel also
+ * tries its per-face form (one thread per face evaluating every edge point,
+ * reported as a negative block size).  Synchronizes; the step
  * graph is recaptured on the next advance. */
 dg_status dg_batch_autotune(dg_batch *b, int n_iter);
 /* Current block sizes: out[3*g + k], k = 0 E-step, 1 face, 2 volume; returns

@@ -110,13 +110,21 @@ struct GDrv final : GroupDrv {
         K, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<R>(g.off.geo), b->at<int32_t>(g.off.nbr),
         b->at<int8_t>(g.off.nbrf), b->at<R>(g.off.fn), b->at<R>(g.off.fsj), eo, bct(b));
   }
+  // tile[1] > 0: one thread per face point; < 0: one thread per face (|tile| threads per block)
   void face(dg_batch* b, Group& g, int vin, cudaStream_t s) override {
-    const int K = (int)g.K, F = (int)g.F, T = g.tile[1];
-    const long long n = (long long)F * S::NFQ;
-    face_kernel<DIM, P, R, true><<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
-        K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<int32_t>(g.off.fe1), b->at<int8_t>(g.off.ff1),
-        b->at<int32_t>(g.off.fe2), b->at<int8_t>(g.off.ff2), b->at<R>(g.off.fnrm), b->at<R>(g.off.fsjf),
-        b->at<R>(g.off.wflux), fo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), bct(b));
+    const int K = (int)g.K, F = (int)g.F, T = g.tile[1] > 0 ? g.tile[1] : -g.tile[1];
+    if (g.tile[1] > 0) {
+      const long long n = (long long)F * S::NFQ;
+      face_kernel<DIM, P, R, true, false><<<(unsigned)((n + T - 1) / T), T, 0, s>>>(
+          K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<int32_t>(g.off.fe1), b->at<int8_t>(g.off.ff1),
+          b->at<int32_t>(g.off.fe2), b->at<int8_t>(g.off.ff2), b->at<R>(g.off.fnrm), b->at<R>(g.off.fsjf),
+          b->at<R>(g.off.wflux), fo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), bct(b));
+    } else {
+      face_kernel<DIM, P, R, true, true><<<(unsigned)((F + T - 1) / T), T, 0, s>>>(
+          K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<int32_t>(g.off.fe1), b->at<int8_t>(g.off.ff1),
+          b->at<int32_t>(g.off.fe2), b->at<int8_t>(g.off.ff2), b->at<R>(g.off.fnrm), b->at<R>(g.off.fsjf),
+          b->at<R>(g.off.wflux), fo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), bct(b));
+    }
   }
   void volume(dg_batch* b, Group& g, int vin, int vout, double c0, double c1, cudaStream_t s) override {
     const int K = (int)g.K, F = (int)g.F, T = g.tile[2];
@@ -626,7 +634,7 @@ dg_status dg_batch_autotune(dg_batch* b, int n_iter) {
   dg_status st = check(b);
   if (st != DG_OK) return st;
   if (n_iter < 1) return bfail(b, DG_ERR_ARG, "n_iter >= 1");
-  static const int cand[4] = {32, 64, 128, 256};
+  static const int cand[8] = {32, 64, 128, 256, -32, -64, -128, -256};
   cudaStream_t s = b->stream;
   cudaEvent_t e0, e1;
   BK(cudaEventCreate(&e0));
@@ -639,7 +647,8 @@ dg_status dg_batch_autotune(dg_batch* b, int n_iter) {
     for (int k = 0; k < 3; ++k) {
       float best = 1e30f;
       int best_t = g.tile[k];
-      for (int ci = 0; ci < 4; ++ci) {
+      const int ncand = k == 1 ? 8 : 4;  // the face kernel also tries its per-face form
+      for (int ci = 0; ci < ncand; ++ci) {
         g.tile[k] = cand[ci];
         auto launch = [&]() {
           if (k == 0) g.drv->estep(b, g, 0, s);
@@ -719,8 +728,10 @@ dg_status dg_batch_tiles(const dg_batch* b, int32_t* out, int cap, int32_t* n_gr
 
 dg_status dg_batch_set_tiles(dg_batch* b, const int32_t* tiles, int n) {
   if (!b || !tiles || n != 3 * (int)b->groups.size()) return bfail(b, DG_ERR_ARG, "need 3 block sizes per group");
-  for (int i = 0; i < n; ++i)
-    if (tiles[i] < 32 || tiles[i] > 256 || tiles[i] % 32) return bfail(b, DG_ERR_ARG, "block sizes must be 32..256, multiples of 32");
+  for (int i = 0; i < n; ++i) {
+    const int v = (i % 3 == 1 && tiles[i] < 0) ? -tiles[i] : tiles[i];
+    if (v < 32 || v > 256 || v % 32) return bfail(b, DG_ERR_ARG, "block sizes must be 32..256, multiples of 32 (negative face entry: per-face form)");
+  }
   for (size_t g = 0; g < b->groups.size(); ++g)
     for (int k = 0; k < 3; ++k) b->groups[g].tile[k] = tiles[3 * g + k];
   destroy_graphs(b);

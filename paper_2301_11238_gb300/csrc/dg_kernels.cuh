@@ -340,7 +340,57 @@ __global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__
     for (int a = 0; a < NP; ++a) E[c * KN + (size_t)e * NP + a] = Eo[c][a];
 }
 
-template <int DIM, int P, typename R, bool BATCH>
+// Numerical flux at one face point m from the traces of both sides at the
+// face nodes (owner's node order along its face); writes the weighted flux.
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void face_point(int m, const R (&Tm)[Sh<DIM, P>::NV + Sh<DIM, P>::NE][Sh<DIM, P>::NFP],
+                                           const R (&Tp)[Sh<DIM, P>::NV + Sh<DIM, P>::NE][Sh<DIM, P>::NFP],
+                                           bool interior, const BCEntry<R>* __restrict__ bct, int bc,
+                                           const R* n, R wsj, const FaceOps<DIM, P, R>& ops, const Phys<R>& ph,
+                                           R* __restrict__ wflux, size_t FQ, size_t t) {
+  using S = Sh<DIM, P>;
+  constexpr int NFP = S::NFP, NV = S::NV, NE = S::NE;
+  R Vm[NV], Vp[NV], Em[NE], Ep[NE];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    R a = R(0), b = R(0);
+#pragma unroll
+    for (int k = 0; k < NFP; ++k) {
+      a += ops.Lf[m * NFP + k] * Tm[v][k];
+      b += ops.Lf[m * NFP + k] * Tp[v][k];
+    }
+    Vm[v] = a;
+    Vp[v] = b;
+  }
+#pragma unroll
+  for (int c = 0; c < NE; ++c) {
+    R a = R(0), b = R(0);
+#pragma unroll
+    for (int k = 0; k < NFP; ++k) {
+      a += ops.Lf[m * NFP + k] * Tm[NV + c][k];
+      b += ops.Lf[m * NFP + k] * Tp[NV + c][k];
+    }
+    Em[c] = a;
+    Ep[c] = b;
+  }
+  if (!interior) {
+    const BCEntry<R> b = bct[bc];
+    ghost_V<DIM, R>(Vm, n, b, Vp);
+    ghost_E<DIM, R>(Em, b, Ep);
+  }
+  R Fn[NV], Qm[NV], Qp[NV];
+  hll<DIM, R>(Vm, Vp, n, ph, Fn);
+  q_normal<DIM, R>(Vm[0], Em, n, ph, Qm);
+  q_normal<DIM, R>(Vp[0], Ep, n, ph, Qp);
+  const R w = ops.wf[m] * wsj;
+#pragma unroll
+  for (int v = 0; v < NV; ++v) wflux[v * FQ + t] = w * (Fn[v] - R(0.5) * (Qm[v] + Qp[v]));
+}
+
+// PERFACE = false: one thread per face point (re-reads the face-node traces
+// for every point); PERFACE = true: one thread per face, traces read once
+// and all edge points evaluated in turn.  Same arithmetic per point.
+template <int DIM, int P, typename R, bool BATCH, bool PERFACE>
 __global__ void __launch_bounds__(256) face_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E,
                                                    const int32_t* __restrict__ fe1, const int8_t* __restrict__ ff1,
                                                    const int32_t* __restrict__ fe2, const int8_t* __restrict__ ff2,
@@ -351,57 +401,53 @@ __global__ void __launch_bounds__(256) face_kernel(int K, int F, const R* __rest
                                                    const BCEntry<R>* __restrict__ bct) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV, NE = S::NE;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= F * NFQ) return;
-  const int fc = t / NFQ, m = t - fc * NFQ;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthreads = PERFACE ? (long long)F : (long long)F * NFQ;
+  if (tid >= nthreads) return;
+  const int fc = PERFACE ? (int)tid : (int)(tid / NFQ);
+  const int m0 = PERFACE ? 0 : (int)(tid - (long long)fc * NFQ);
   const size_t KN = (size_t)K * NP;
   const int e1 = fe1[fc], f1 = ff1[fc], e2 = fe2[fc];
   const Phys<R> ph = BATCH ? ptab[inst[e1]] : ph0;
   R n[DIM];
 #pragma unroll
   for (int i = 0; i < DIM; ++i) n[i] = fnrm[(size_t)i * F + fc];
-  R Vm[NV], Vp[NV], Em[NE], Ep[NE];
-#pragma unroll
-  for (int v = 0; v < NV; ++v) Vm[v] = R(0);
-#pragma unroll
-  for (int c = 0; c < NE; ++c) Em[c] = R(0);
+  R Tm[NV + NE][NFP], Tp[NV + NE][NFP];
 #pragma unroll
   for (int k = 0; k < NFP; ++k) {
-    const R L = ops.Lf[m * NFP + k];
     const size_t a = (size_t)e1 * NP + ops.fmask[f1 * NFP + k];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Vm[v] += L * V[v * KN + a];
+    for (int v = 0; v < NV; ++v) Tm[v][k] = V[v * KN + a];
 #pragma unroll
-    for (int c = 0; c < NE; ++c) Em[c] += L * E[c * KN + a];
+    for (int c = 0; c < NE; ++c) Tm[NV + c][k] = E[c * KN + a];
   }
-  if (e2 >= 0) {
+  const bool interior = e2 >= 0;
+  if (interior) {
     const int f2 = ff2[fc];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Vp[v] = R(0);
-#pragma unroll
-    for (int c = 0; c < NE; ++c) Ep[c] = R(0);
-#pragma unroll
     for (int k = 0; k < NFP; ++k) {
-      const R L = ops.Lf[m * NFP + k];
       const size_t b = (size_t)e2 * NP + ops.fmask[f2 * NFP + (NFP - 1 - k)];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Vp[v] += L * V[v * KN + b];
+      for (int v = 0; v < NV; ++v) Tp[v][k] = V[v * KN + b];
 #pragma unroll
-      for (int c = 0; c < NE; ++c) Ep[c] += L * E[c * KN + b];
+      for (int c = 0; c < NE; ++c) Tp[NV + c][k] = E[c * KN + b];
     }
   } else {
-    const BCEntry<R> bc = bct[-1 - e2];
-    ghost_V<DIM, R>(Vm, n, bc, Vp);
-    ghost_E<DIM, R>(Em, bc, Ep);
-  }
-  R Fn[NV], Qm[NV], Qp[NV];
-  hll<DIM, R>(Vm, Vp, n, ph, Fn);
-  q_normal<DIM, R>(Vm[0], Em, n, ph, Qm);
-  q_normal<DIM, R>(Vp[0], Ep, n, ph, Qp);
-  const R w = ops.wf[m] * fsj[fc];
-  const size_t FQ = (size_t)F * NFQ;
 #pragma unroll
-  for (int v = 0; v < NV; ++v) wflux[v * FQ + t] = w * (Fn[v] - R(0.5) * (Qm[v] + Qp[v]));
+    for (int r = 0; r < NV + NE; ++r)
+#pragma unroll
+      for (int k = 0; k < NFP; ++k) Tp[r][k] = Tm[r][k];
+  }
+  const R wsj = fsj[fc];
+  const size_t FQ = (size_t)F * NFQ;
+  if (PERFACE) {
+#pragma unroll 1
+    for (int m = 0; m < NFQ; ++m)
+      face_point<DIM, P, R>(m, Tm, Tp, interior, bct, -1 - e2, n, wsj, ops, ph, wflux, FQ,
+                            (size_t)fc * NFQ + m);
+  } else {
+    face_point<DIM, P, R>(m0, Tm, Tp, interior, bct, -1 - e2, n, wsj, ops, ph, wflux, FQ, (size_t)tid);
+  }
 }
 
 // mode 0: write dV/dt to out; mode 1: out = c0 * V0 + c1 * (Vin + dt * dV/dt).
@@ -583,7 +629,11 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
       for (int j = 0; j < DIM; ++j) rhs[j][a] -= wd * uq[j] * la;
     }
   }
-  // Cholesky of the reference-scaled M_h (lower triangle)
+  // Cholesky of the reference-scaled M_h (lower triangle); the diagonal is
+  // kept as reciprocals so the factorization and both triangular solves
+  // multiply instead of divide (NP divisions per element instead of
+  // NP (NP + 3) / 2 + 2 DIM NP).
+  R dinv[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
 #pragma unroll
@@ -591,12 +641,12 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
       R s = Mh[a][b];
 #pragma unroll
       for (int c = 0; c < b; ++c) s -= Mh[a][c] * Mh[b][c];
-      Mh[a][b] = s / Mh[b][b];
+      Mh[a][b] = s * dinv[b];
     }
     R d = Mh[a][a];
 #pragma unroll
     for (int c = 0; c < a; ++c) d -= Mh[a][c] * Mh[a][c];
-    Mh[a][a] = sqrt(d);
+    dinv[a] = R(1) / sqrt(d);
   }
 #pragma unroll
   for (int j = 0; j < DIM; ++j) {
@@ -606,14 +656,14 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
       R s = rhs[j][a];
 #pragma unroll
       for (int c = 0; c < a; ++c) s -= Mh[a][c] * y[c];
-      y[a] = s / Mh[a][a];
+      y[a] = s * dinv[a];
     }
 #pragma unroll
     for (int a = NP - 1; a >= 0; --a) {
       R s = y[a];
 #pragma unroll
       for (int c = a + 1; c < NP; ++c) s -= Mh[c][a] * dV[1 + j][c];
-      dV[1 + j][a] = s / Mh[a][a];
+      dV[1 + j][a] = s * dinv[a];
     }
   }
 
@@ -678,9 +728,10 @@ __global__ void __launch_bounds__(256) dt_partial_kernel(int K, const R* __restr
       if (!isfinite(l) || !isfinite(h)) bad = true;
       lam = fmax(lam, l);
     }
-    const double dx = (double)geo[5 * K + e];
-    const double qq = 2.0 * P + 1.0;
-    dte = cfl * dx / (qq * (double)lam + qq * qq * 2.0 * nu / dx);
+    // per-element bound in the state's precision; min and time sum in FP64
+    const R dx = geo[5 * K + e];
+    const R qq = R(2 * P + 1);
+    dte = (double)((R)cfl * dx / (qq * lam + qq * qq * R(2) * (R)nu / dx));
     if (bad) dte = -1.0;
   }
   double v = warp_min(dte);
@@ -797,9 +848,10 @@ __global__ void __launch_bounds__(256) dt_block_kernel(int K, const int64_t* __r
       if (!isfinite(l) || !isfinite(h)) bad = true;
       lam = fmax(lam, l);
     }
-    const double dx = (double)geo[5 * K + e];
-    const double qq = 2.0 * P + 1.0;
-    dte = cfl * dx / (qq * (double)lam + qq * qq * 2.0 * nu / dx);
+    // per-element bound in the state's precision; min and time sum in FP64
+    const R dx = geo[5 * K + e];
+    const R qq = R(2 * P + 1);
+    dte = (double)((R)cfl * dx / (qq * lam + qq * qq * R(2) * (R)nu / dx));
     if (bad) dte = -1.0;
   }
   double v = warp_min(dte);

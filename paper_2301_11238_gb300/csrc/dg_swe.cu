@@ -109,7 +109,7 @@ struct Impl final : Driver {
   void face(dg_swe_ctx* c, const void* V, const void* E, cudaStream_t s) override {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     const long long n = (long long)F * S::NFQ;
-    face_kernel<DIM, P, R, false><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+    face_kernel<DIM, P, R, false, false><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
         K, F, (const R*)V, (const R*)E, c->at<int32_t>(c->off.fe1), c->at<int8_t>(c->off.ff1),
         c->at<int32_t>(c->off.fe2), c->at<int8_t>(c->off.ff2), c->at<R>(c->off.fnrm), c->at<R>(c->off.fsjf),
         c->at<R>(c->off.wflux), fo, ph, nullptr, nullptr, c->at<BCEntry<R>>(c->off.bct));
@@ -125,7 +125,7 @@ struct Impl final : Driver {
   void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) override {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     const long long n = (long long)F * S::NFQ;
-    face_kernel<DIM, P, R, false><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
+    face_kernel<DIM, P, R, false, false><<<(unsigned)((n + kBlock - 1) / kBlock), kBlock, 0, s>>>(
         K, F, (const R*)V, (const R*)E, c->at<int32_t>(c->off.fe1), c->at<int8_t>(c->off.ff1),
         c->at<int32_t>(c->off.fe2), c->at<int8_t>(c->off.ff2), c->at<R>(c->off.fnrm), c->at<R>(c->off.fsjf),
         (R*)wflux, fo, ph, nullptr, nullptr, c->at<BCEntry<R>>(c->off.bct));
