@@ -481,6 +481,15 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
   for (int v = 0; v < NV; ++v)
 #pragma unroll
     for (int a = 0; a < NP; ++a) r[v][a] = R(0);
+  // the element's nodal values, read once (each is used at every volume point)
+  R Vn[NV][NP], En[NE][NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Vn[v][a] = Vin[v * KN + eo + a];
+#pragma unroll
+    for (int c = 0; c < NE; ++c) En[c][a] = E[c * KN + eo + a];
+  }
 
   // ---- volume integrals: -<grad N, F - Q> - <N, S>  (Eq. WeakForm51)
 #pragma unroll 1
@@ -495,9 +504,9 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
     for (int a = 0; a < NP; ++a) {
       const R l = ops.Vq[q * NP + a];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Vq[v] += l * Vin[v * KN + eo + a];
+      for (int v = 0; v < NV; ++v) Vq[v] += l * Vn[v][a];
 #pragma unroll
-      for (int c = 0; c < NE; ++c) Eq[c] += l * E[c * KN + eo + a];
+      for (int c = 0; c < NE; ++c) Eq[c] += l * En[c][a];
       if (bed) {
         const R H = bed[eo + a];
         Hr += ops.Drq[q * NP + a] * H;
@@ -612,10 +621,10 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
       const R l = ops.Vq[q * NP + a];
-      hq += l * Vin[eo + a];
+      hq += l * Vn[0][a];
       hdq += l * dV[0][a];
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) uq[j] += l * Vin[(1 + j) * KN + eo + a];
+      for (int j = 0; j < DIM; ++j) uq[j] += l * Vn[1 + j][a];
     }
     const R wh = ops.wq[q] * fmax(hq, ph.h_floor);
     const R wd = ops.wq[q] * hdq;
@@ -679,7 +688,7 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
-        const R vi = Vin[v * KN + eo + a];
+        const R vi = Vn[v][a];
         R y = c1 * (vi + dt * dV[v][a]);
         if (c0 != R(0)) y += c0 * V0[v * KN + eo + a];
         out[v * KN + eo + a] = y;

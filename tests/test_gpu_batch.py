@@ -63,7 +63,8 @@ def test_autotune_keeps_results():
     B1, _ = G.batch_from_cases(cases)
     B2, _ = G.batch_from_cases(cases)
     tiles = B2.autotune(3)
-    assert all(t in (32, 64, 128, 256) for g in tiles for t in g)
+    # per-face form of the face kernel is reported as a negative block size
+    assert all(abs(t) in (32, 64, 128, 256) and (t > 0 or k == 1) for g in tiles for k, t in enumerate(g))
     B1.run(10)
     B2.run(10)
     for i in range(len(cases)):
