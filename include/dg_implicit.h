@@ -13,10 +13,11 @@
  * uses the Appendix A tangent terms with the HLL wave speeds held fixed; it
  * is block tridiagonal for a left-to-right ordered mesh (element e's right
  * neighbour is e + 1) and is solved by block Thomas elimination with partial
- * pivoting (the paper does not name its linear solver).  Newton stops when
+ * pivoting (the paper does not name its linear solver), either in FP64 or
+ * factored in FP32 and refined in FP64 (linear_solver).  Newton stops when
  * ||R||_2 <= rtol ||R^0||_2, ||R||_2 <= atol or
  * ||dx||_inf <= xtol (1 + ||x||_inf), after at most max_it iterations
- * (the paper uses 10, Sec. 6).  Everything is FP64.
+ * (the paper uses 10, Sec. 6).  Residual and Jacobian are FP64.
  *
  * The whole integration (time steps x Newton iterations: assembly, solve,
  * update, convergence test) runs in one persistent launch with one thread
@@ -41,6 +42,11 @@ typedef struct {
   int32_t on_fail_continue;  /* 1: keep going after max_it (the paper's runs);
                                 0: stop and report DG_ERR_NEWTON                  */
   double rtol, atol, xtol;   /* stopping rule above                               */
+  int32_t linear_solver;     /* 0: FP64 block Thomas (partial pivoting);
+                                1: FP32 block-Thomas factorization with two FP64
+                                   iterative-refinement rounds (residual of the
+                                   linear system in FP64); needs
+                                   2(p+1) + m3 + 1 <= 10                           */
 } dg_implicit_params;
 
 typedef struct {

@@ -36,8 +36,11 @@ struct ImplArgs {
   int reg;
   double rtol, atol, xtol;
   int max_it, on_fail_continue;
+  int mixed;  // 1: FP32 block-Thomas factorization + FP64 iterative refinement
   BCEntry<double> bcL, bcR;
   double *X, *Uold, *R, *D, *L, *U, *W, *Y, *DX;
+  float *Wf, *Af;    // mixed: W_e = A_e^-1 U_e and A_e^-1 per element (FP32)
+  double *Rr, *Dx2;  // mixed: refinement residual and correction
   const double *J, *bed;
   double* red;  // per-block partials of the residual norm / dx norms
   dg_implicit_stats* st;
@@ -441,6 +444,155 @@ __device__ void thomas_warp(int K, const ImplArgs& a) {
   }
 }
 
+// Mixed-precision block Thomas, factorization (one warp): lane c owns
+// column c of [A_e | U_e | I] in FP32 (3 NB <= 32 columns) with
+// A_e = D_e - L_e W_{e-1}; Gauss-Jordan leaves W_e = A_e^-1 U_e on lanes
+// NB..2NB-1 and A_e^-1 on lanes 2NB..3NB-1, both stored.
+template <int NB>
+__device__ void thomas_factor_f32(int K, const ImplArgs& a) {
+  const int lane = threadIdx.x & 31;
+  float col[NB];
+#pragma unroll
+  for (int r = 0; r < NB; ++r) col[r] = 0.f;
+  for (int e = 0; e < K; ++e) {
+    const double* D = a.D + (size_t)e * NB * NB;
+    const double* L = a.L + (size_t)e * NB * NB;
+    const double* U = a.U + (size_t)e * NB * NB;
+    float prev[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) prev[j] = __shfl_sync(0xffffffffu, col[j], lane < NB ? NB + lane : lane);
+#pragma unroll
+    for (int r = 0; r < NB; ++r) {
+      float v = 0.f;
+      if (lane < NB) {
+        v = (float)D[r * NB + lane];
+        if (e > 0) {
+          float sacc = 0.f;
+#pragma unroll
+          for (int j = 0; j < NB; ++j) sacc += (float)L[r * NB + j] * prev[j];
+          v -= sacc;
+        }
+      } else if (lane < 2 * NB) {
+        v = (float)U[r * NB + (lane - NB)];
+      } else if (lane < 3 * NB) {
+        v = (r == lane - 2 * NB) ? 1.f : 0.f;
+      }
+      col[r] = v;
+    }
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+      int piv = k;
+      float best = fabsf(col[k]);
+#pragma unroll
+      for (int r = k + 1; r < NB; ++r)
+        if (fabsf(col[r]) > best) {
+          best = fabsf(col[r]);
+          piv = r;
+        }
+      piv = __shfl_sync(0xffffffffu, piv, k);
+#pragma unroll
+      for (int r = k + 1; r < NB; ++r)
+        if (r == piv) {
+          const float t = col[k];
+          col[k] = col[r];
+          col[r] = t;
+        }
+      const float pv = __shfl_sync(0xffffffffu, col[k], k);
+      col[k] = col[k] / pv;
+#pragma unroll
+      for (int r = 0; r < NB; ++r) {
+        if (r == k) continue;
+        const float fct = __shfl_sync(0xffffffffu, col[r], k);
+        col[r] -= fct * col[k];
+      }
+    }
+    if (lane >= NB && lane < 3 * NB) {
+      float* dst = lane < 2 * NB ? a.Wf + ((size_t)e * NB + (lane - NB)) * NB
+                                 : a.Af + ((size_t)e * NB + (lane - 2 * NB)) * NB;
+#pragma unroll
+      for (int r = 0; r < NB; ++r) dst[r] = col[r];  // column-major blocks
+    }
+  }
+}
+
+// Solve J x = b with the stored FP32 factors (one warp; lane r < NB owns row
+// r): forward y_e = A_e^-1 (b_e - L_e y_{e-1}), back x_e = y_e - W_e x_{e+1}.
+// b and x are FP64 arrays [K][NB]; y is kept in a.Y.
+template <int NB>
+__device__ void thomas_apply_f32(int K, const ImplArgs& a, const double* b, double* x) {
+  const int lane = threadIdx.x & 31;
+  float yp[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) yp[j] = 0.f;
+  for (int e = 0; e < K; ++e) {
+    float t = 0.f;
+    if (lane < NB) {
+      t = (float)b[(size_t)e * NB + lane];
+      if (e > 0) {
+        const double* L = a.L + (size_t)e * NB * NB + (size_t)lane * NB;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) t -= (float)L[j] * yp[j];
+      }
+    }
+    float tt[NB];
+#pragma unroll
+    for (int j = 0; j < NB; ++j) tt[j] = __shfl_sync(0xffffffffu, t, j);
+    float y = 0.f;
+    if (lane < NB) {
+      const float* Ai = a.Af + (size_t)e * NB * NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) y += Ai[j * NB + lane] * tt[j];
+      a.Y[(size_t)e * NB + lane] = (double)y;
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) yp[j] = __shfl_sync(0xffffffffu, y, j);
+  }
+  __syncwarp();
+  float nx[NB];
+#pragma unroll
+  for (int j = 0; j < NB; ++j) nx[j] = 0.f;
+  for (int e = K - 1; e >= 0; --e) {
+    float v = 0.f;
+    if (lane < NB) {
+      v = (float)a.Y[(size_t)e * NB + lane];
+      if (e < K - 1) {
+        const float* Wm = a.Wf + (size_t)e * NB * NB;
+#pragma unroll
+        for (int j = 0; j < NB; ++j) v -= Wm[j * NB + lane] * nx[j];
+      }
+      x[(size_t)e * NB + lane] = (double)v;
+    }
+#pragma unroll
+    for (int j = 0; j < NB; ++j) nx[j] = __shfl_sync(0xffffffffu, v, j);
+  }
+}
+
+// FP64 residual of the linear system, r = -R - J dx (block tridiagonal), all threads.
+template <int NB>
+__device__ void linear_residual_f64(int K, const ImplArgs& a) {
+  for (int i = threadIdx.x; i < K * NB; i += blockDim.x) {
+    const int e = i / NB, r = i - e * NB;
+    double v = -a.R[i];
+    const double* D = a.D + (size_t)e * NB * NB + (size_t)r * NB;
+    const double* x = a.DX + (size_t)e * NB;
+#pragma unroll
+    for (int j = 0; j < NB; ++j) v -= D[j] * x[j];
+    if (e > 0) {
+      const double* L = a.L + (size_t)e * NB * NB + (size_t)r * NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) v -= L[j] * x[j - NB];
+    }
+    if (e < K - 1) {
+      const double* U = a.U + (size_t)e * NB * NB + (size_t)r * NB;
+#pragma unroll
+      for (int j = 0; j < NB; ++j) v -= U[j] * x[j + NB];
+    }
+    a.Rr[i] = v;
+  }
+}
+
+constexpr int kRefinements = 2;
+
 template <int P, int M3>
 __global__ void __launch_bounds__(256) implicit_kernel(ImplArgs a, ImplOps<P, M3> o, long long n_steps) {
   using S = IS<P, M3>;
@@ -492,8 +644,33 @@ __global__ void __launch_bounds__(256) implicit_kernel(ImplArgs a, ImplOps<P, M3
         break;
       }
       __syncthreads();
-      if (threadIdx.x < 32) thomas_warp<NB>(K, a);
-      __syncthreads();
+      if constexpr (3 * NB <= 32) {
+        if (a.mixed) {
+          // -R into Rr, FP32 factor + solve, then FP64 residual / correction rounds
+          for (int i = threadIdx.x; i < K * NB; i += blockDim.x) a.Rr[i] = -a.R[i];
+          __syncthreads();
+          if (threadIdx.x < 32) {
+            thomas_factor_f32<NB>(K, a);
+            __syncwarp();
+            thomas_apply_f32<NB>(K, a, a.Rr, a.DX);
+          }
+          __syncthreads();
+          for (int ref = 0; ref < kRefinements; ++ref) {
+            linear_residual_f64<NB>(K, a);
+            __syncthreads();
+            if (threadIdx.x < 32) thomas_apply_f32<NB>(K, a, a.Rr, a.Dx2);
+            __syncthreads();
+            for (int i = threadIdx.x; i < K * NB; i += blockDim.x) a.DX[i] += a.Dx2[i];
+            __syncthreads();
+          }
+        } else {
+          if (threadIdx.x < 32) thomas_warp<NB>(K, a);
+          __syncthreads();
+        }
+      } else {
+        if (threadIdx.x < 32) thomas_warp<NB>(K, a);
+        __syncthreads();
+      }
       double dm = 0.0, xm = 0.0;
       for (int i = threadIdx.x; i < K * NB; i += blockDim.x) {
         const double d = a.DX[i];
@@ -627,7 +804,7 @@ struct dg_implicit {
   size_t ws_need = 0;
   char* ws = nullptr;
   struct {
-    size_t X, Uold, R, D, L, U, W, Y, DX, J, bed, red, st, MEinv, act;
+    size_t X, Uold, R, D, L, U, W, Y, DX, J, bed, red, st, MEinv, act, Wf, Af, Rr, Dx2;
   } off{};
   cudaStream_t stream = nullptr;
   std::unique_ptr<ImplDrv> drv;
@@ -670,6 +847,11 @@ ImplArgs make_args(dg_implicit* s) {
   a.xtol = s->ip.xtol;
   a.max_it = s->ip.max_it;
   a.on_fail_continue = s->ip.on_fail_continue;
+  a.mixed = s->ip.linear_solver == 1 ? 1 : 0;
+  a.Wf = s->at<float>(s->off.Wf);
+  a.Af = s->at<float>(s->off.Af);
+  a.Rr = s->at<double>(s->off.Rr);
+  a.Dx2 = s->at<double>(s->off.Dx2);
   a.bcL = s->bcL;
   a.bcR = s->bcR;
   a.X = s->at<double>(s->off.X);
@@ -771,9 +953,13 @@ dg_status dg_implicit_init(const dg_swe_mesh* mesh, int order, int regularizatio
     return ifail(*out, DG_ERR_UNSUPPORTED, "the implicit integrator is one-dimensional");
   }
   const int m3 = ip->m3 < 0 ? order : ip->m3;
-  if (!(ip->dt > 0) || ip->max_it < 1 || m3 < 0 || m3 > order) {
+  if (!(ip->dt > 0) || ip->max_it < 1 || m3 < 0 || m3 > order || ip->linear_solver < 0 || ip->linear_solver > 1) {
     *out = s.release();
-    return ifail(*out, DG_ERR_ARG, "need dt > 0, max_it >= 1 and 0 <= m3 <= order");
+    return ifail(*out, DG_ERR_ARG, "need dt > 0, max_it >= 1, 0 <= m3 <= order, linear_solver in {0, 1}");
+  }
+  if (ip->linear_solver == 1 && 3 * (2 * (order + 1) + m3 + 1) > 32) {
+    *out = s.release();
+    return ifail(*out, DG_ERR_UNSUPPORTED, "the FP32 factorization handles blocks of at most 10 unknowns (2(p+1) + m3 + 1 <= 10)");
   }
   dg_swe_ctx* c = nullptr;
   dg_status st = dg_swe_init(mesh, order, regularization, params, &c);
@@ -900,6 +1086,10 @@ dg_status dg_implicit_init(const dg_swe_mesh* mesh, int order, int regularizatio
   s->off.st = take(sizeof(dg_implicit_stats));
   s->off.MEinv = take(NE * NE * 8);
   s->off.act = take(8);
+  s->off.Wf = take(K * NB * NB * 4);
+  s->off.Af = take(K * NB * NB * 4);
+  s->off.Rr = take(K * NB * 8);
+  s->off.Dx2 = take(K * NB * 8);
   s->ws_need = off;
   *out = s.release();
   return DG_OK;

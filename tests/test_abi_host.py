@@ -95,3 +95,11 @@ def test_calls_without_workspace_fail_cleanly():
     st = s.L.dg_swe_set_workspace(s.ctx, C.c_void_p(0x1001), s.workspace_bytes)
     assert st == G.DG_ERR_WORKSPACE  # misaligned
     s.close()
+
+
+def test_empty_mesh_rejected():
+    import paper_2301_11238_gb300 as G
+    coords = np.array([[0.0], [1.0]])
+    with pytest.raises(G.DGError) as ei:
+        G.Solver(1, coords, np.zeros((0, 2), dtype=np.int32), 1, 0, synth.cases.default_params(), allocate=False)
+    assert ei.value.status == G.DG_ERR_ARG

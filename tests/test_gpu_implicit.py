@@ -111,3 +111,38 @@ def test_newton_failure_is_reported():
     with pytest.raises(G.DGError) as ei:
         s.run(3)
     assert ei.value.status == G.DG_ERR_NEWTON
+
+
+def _gpu_mixed(case, dt, n):
+    import paper_2301_11238_gb300 as G
+    s, V0 = G.implicit_from_case(case, dt=dt, mixed=True)
+    its = []
+    for _ in range(n):
+        its.append(s.run(1)["last_its"])
+    V, _ = s.get_state()
+    return s, V, its
+
+
+def test_mixed_precision_solve_matches_oracle_dam_break():
+    """FP32 block-Thomas factorization + two FP64 refinement rounds: the
+    Newton iterates match the FP64 oracle's (iteration counts within one,
+    states within 1e-12)."""
+    c = synth.paper_dam_break_1d(n_el=100, order=1, m3=0, gamma=1e2, beta=1e2)
+    d, im, X, Vo, its_o = _oracle_run(c, 1e-6, 20)
+    s, V, its_g = _gpu_mixed(c, 1e-6, 20)
+    assert all(abs(a - b) <= 1 for a, b in zip(its_g, its_o))
+    assert rel_l2(V, Vo) < 1e-12
+
+
+def test_mixed_precision_solve_yield_and_p2():
+    c = synth.parallel_surface_1d(n_el=100, order=1, reg=3, gamma=1e3, m3=1)
+    d, im, X, Vo, its_o = _oracle_run(c, 0.1, 10)
+    s, V, its_g = _gpu_mixed(c, 0.1, 10)
+    assert all(abs(a - b) <= 1 for a, b in zip(its_g, its_o))
+    assert rel_l2(V, Vo) < 1e-10
+    c2 = synth.paper_dam_break_1d(n_el=50, order=2, m3=1, reg=3, gamma=5.0, sigma0=0.5)
+    h_fn, u_fn, _ = synth.random_smooth_fields(1, 19, h_amp=0.3, u_amp=0.5)
+    c2.h_fn, c2.u_fn = h_fn, u_fn
+    d, im, X, Vo, its_o = _oracle_run(c2, 2e-4, 5)
+    s, V, its_g = _gpu_mixed(c2, 2e-4, 5)
+    assert rel_l2(V, Vo) < 1e-11

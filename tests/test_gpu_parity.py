@@ -200,3 +200,53 @@ def test_residual_fp64_fine_1d_within_rounding_sensitivity():
     sens = sensitivity(d, V0)[0]
     assert sens > FP64_TOL
     assert rel_l2(dv.cpu().numpy(), dv_o) < 10.0 * sens
+
+
+# ------------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("dim", [1, 2])
+def test_single_element_and_smallest_meshes(dim):
+    """Every face a boundary face (1D, one element) or two triangles sharing
+    one face (2D, one square): residual and a few steps against the oracle."""
+    if dim == 1:
+        c = smooth_case(1, 3, 3, n=1, seed=2, bc="dirichlet")
+    else:
+        c = smooth_case(2, 2, 1, n=1, seed=2, bc="wall")
+    d, V0, _, s = both(c)
+    dv_o, E_o = residual_nodal(d, V0)
+    dv, E = s.residual(V0)
+    check(dv, E, dv_o, E_o, fp64_tol(d, V0))
+    Vo, _, _ = run_explicit(d, V0, 3)
+    s.set_state(V0)
+    s.run(3)
+    V, _ = s.get_state()
+    assert rel_l2(V, Vo) < FP64_TOL
+
+
+@pytest.mark.parametrize("reg", [1, 2, 3, 4, 5])
+def test_zero_yield_stress_is_newtonian(reg):
+    """sigma0 = 0 removes the Bingham term for every regularization: the
+    library's residual equals its Newtonian residual bit for bit."""
+    import paper_2301_11238_gb300 as G
+    c = smooth_case(2, 2, reg, n=6, seed=4, sigma0=0.0)
+    c0 = smooth_case(2, 2, 0, n=6, seed=4, sigma0=0.0)
+    _, V0, bed, s = both(c)
+    _, _, _, s0 = both(c0)
+    dv, E = s.residual(V0)
+    dv0, E0 = s0.residual(V0)
+    assert np.array_equal(dv.cpu().numpy(), dv0.cpu().numpy())
+
+
+def test_near_dry_state_uses_floor():
+    """Depths below h_floor (1e-6) at some nodes: wave speeds and the
+    h-weighted mass use max(h, h_floor); the result stays finite and matches
+    the oracle."""
+    c = smooth_case(2, 2, 3, n=6, seed=5, bed=False)
+    c.params["h_floor"] = 1e-3
+    d, V0, _, s = both(c)
+    V = V0.copy()
+    V[0, :5, :] = 2e-4  # five elements below the floor
+    dv_o, E_o = residual_nodal(d, V)
+    dv, E = s.residual(V)
+    assert np.isfinite(dv.cpu().numpy()).all()
+    check(dv, E, dv_o, E_o, fp64_tol(d, V))
