@@ -136,6 +136,26 @@ def workload_name(args):
         args.workload]
 
 
+
+# ---------------------------------------------------------------- multi-rank aggregation
+
+def max_over_ranks(x, device="cpu"):
+    """Largest value of x over all ranks (the slowest rank's time); x itself
+    without an initialised multi-rank process group."""
+    import torch
+    import torch.distributed as dist
+    if not dist.is_available() or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_throughput(units_per_rank_step, steps, world, max_ms):
+    """Units processed by all ranks divided by the slowest rank's time (weak
+    scaling: every rank runs its own replica of the workload)."""
+    return units_per_rank_step * steps * world / (max_ms / 1e3)
+
 # ---------------------------------------------------------------- analytic counts
 
 def shape(dim, p):
@@ -495,12 +515,8 @@ def main():
             stream.synchronize()
         barrier()
     ms = [a.elapsed_time(b) for a, b in evs]
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = units_per_step * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(sum(ms), device="cuda")
+    value = whole_job_throughput(units_per_step, args.steps, world, total_ms)
     stats = batch.stats() if batch is not None else [s.sync() for s in solvers]
 
     # ---- dominant kernel: live per-launch timing on the launching stream

@@ -47,6 +47,13 @@ typedef struct {
                                    iterative-refinement rounds (residual of the
                                    linear system in FP64); needs
                                    2(p+1) + m3 + 1 <= 10                           */
+  int32_t n_gamma;           /* > 1: continuation in the regularization parameter
+                                within every time step (Sec. 6.3): Newton is run in
+                                turn for gamma_i = gamma0 + (i-1)(gamma - gamma0)
+                                / (n_gamma - 1), i = 1..n_gamma, each stage from
+                                the previous stage's solution; iterations of all
+                                stages are counted; <= 1: plain Newton            */
+  double gamma0;             /* first continuation value (> 0 when n_gamma > 1)   */
 } dg_implicit_params;
 
 typedef struct {

@@ -228,9 +228,12 @@ class Implicit1D:
         """E consistent with V: solve R_E = 0 for E (it is linear in E)."""
         return self.d.e_step(Vh)
 
-    def step(self, X, max_it=10, rtol=1e-10, atol=1e-13, xtol=1e-14):
-        """One backward-Euler step from X (K, nb); returns (X_new, iterations, converged)."""
-        Vh_old, _ = self.unpack(X)
+    def step(self, X, max_it=10, rtol=1e-10, atol=1e-13, xtol=1e-14, Vh_old=None):
+        """One backward-Euler step from X (K, nb); returns (X_new, iterations,
+        converged).  ``Vh_old`` overrides the previous time level (continuation
+        stages start from a later iterate)."""
+        if Vh_old is None:
+            Vh_old, _ = self.unpack(X)
         Uold = self.old_term(Vh_old)
         Xk = X.copy()
         R = self.residual(Xk, Uold)
@@ -246,6 +249,28 @@ class Implicit1D:
             if rn <= rtol * r0 or rn <= atol or np.abs(dx).max() <= xtol * (1 + np.abs(Xk).max()):
                 return Xk, it, True
         return Xk, max_it, False
+
+    def step_continuation(self, X, n_gamma, gamma0, **kw):
+        """One step with continuation in the regularization parameter
+        (Sec. 6.3): Newton is solved in turn for
+        gamma_i = gamma0 + (i - 1)(gamma - gamma0)/(n_gamma - 1), i = 1..n_gamma,
+        each stage starting from the previous stage's solution; the time term
+        keeps U(V^{k-1}).  Returns (X, total iterations, all stages converged)."""
+        if n_gamma <= 1:
+            return self.step(X, **kw)
+        gamma = self.prm["gamma"]
+        Vh_old, _ = self.unpack(X)
+        total, ok_all = 0, True
+        Xk = X
+        try:
+            for i in range(1, n_gamma + 1):
+                self.prm["gamma"] = gamma0 + (i - 1) * (gamma - gamma0) / (n_gamma - 1)
+                Xk, it, ok = self.step(Xk, Vh_old=Vh_old, **kw)
+                total += it
+                ok_all = ok_all and ok
+        finally:
+            self.prm["gamma"] = gamma
+        return Xk, total, ok_all
 
     def run(self, Vh0, n_steps, **kw):
         X = self.pack(Vh0, self.initial_E(Vh0))

@@ -372,7 +372,7 @@ class Implicit:
 
     def __init__(self, coords, etov, order, reg, prm, dt, m3=-1, face_bc=None, bcs=None, bed=None,
                  max_it=10, on_fail_continue=True, rtol=1e-10, atol=1e-13, xtol=1e-14, device="cuda",
-                 stream=None, allocate=True, mixed=False):
+                 stream=None, allocate=True, mixed=False, n_gamma=1, gamma0=0.0):
         self.L = _lib.lib()
         self.order = int(order)
         self._coords = np.ascontiguousarray(coords, dtype=np.float64).reshape(-1, 1)
@@ -390,7 +390,7 @@ class Implicit:
         self._params = make_params(prm, bcs, PREC_FP64)
         ip = _lib.ImplicitParams(dt=float(dt), m3=int(m3), max_it=int(max_it),
                                  on_fail_continue=1 if on_fail_continue else 0, rtol=rtol, atol=atol, xtol=xtol,
-                                 linear_solver=1 if mixed else 0)
+                                 linear_solver=1 if mixed else 0, n_gamma=int(n_gamma), gamma0=float(gamma0))
         ctx = C.c_void_p()
         st = self.L.dg_implicit_init(C.byref(m), self.order, int(reg), C.byref(self._params), C.byref(ip),
                                      C.byref(ctx))

@@ -36,7 +36,8 @@ class Stats(C.Structure):
 class ImplicitParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("m3", C.c_int32), ("max_it", C.c_int32),
                 ("on_fail_continue", C.c_int32), ("rtol", C.c_double), ("atol", C.c_double),
-                ("xtol", C.c_double), ("linear_solver", C.c_int32)]
+                ("xtol", C.c_double), ("linear_solver", C.c_int32), ("n_gamma", C.c_int32),
+                ("gamma0", C.c_double)]
 
 
 class ImplicitStats(C.Structure):

@@ -36,6 +36,8 @@ struct ImplArgs {
   int reg;
   double rtol, atol, xtol;
   int max_it, on_fail_continue;
+  int n_gamma;    // > 1: continuation in gamma within each time step (Sec. 6.3)
+  double gamma0;
   int mixed;  // 1: FP32 block-Thomas factorization + FP64 iterative refinement
   BCEntry<double> bcL, bcR;
   double *X, *Uold, *R, *D, *L, *U, *W, *Y, *DX;
@@ -593,6 +595,83 @@ __device__ void linear_residual_f64(int K, const ImplArgs& a) {
 
 constexpr int kRefinements = 2;
 
+// Newton iteration for one time level (and one continuation stage): returns
+// the iteration count, whether it converged and max |x|.
+template <int P, int M3>
+__device__ void newton_solve(const ImplArgs& a, const ImplOps<P, M3>& o, double* sred, int& its_out,
+                             bool& conv_out, double& xmax_out) {
+  using S = IS<P, M3>;
+  constexpr int NB = S::NB;
+  const int K = a.K;
+  double r0 = 0.0, dxmax = 0.0, xmax = 0.0;
+  int its = 0;
+  bool conv = false;
+  for (int it = 0;; ++it) {
+    double part = 0.0;
+    for (int e = threadIdx.x; e < K; e += blockDim.x) part += assemble<P, M3>(e, a, o);
+    const double rn = sqrt(block_sum(part, sred));
+    if (it == 0) {
+      r0 = rn;
+      if (rn <= a.atol) {
+        conv = true;
+        its = 0;
+        break;
+      }
+    } else if (rn <= a.rtol * r0 || rn <= a.atol || dxmax <= a.xtol * (1.0 + xmax)) {
+      conv = true;
+      its = it;
+      break;
+    }
+    if (it == a.max_it || !(rn == rn)) {
+      its = it;
+      break;
+    }
+    __syncthreads();
+    if constexpr (3 * NB <= 32) {
+      if (a.mixed) {
+        // -R into Rr, FP32 factor + solve, then FP64 residual / correction rounds
+        for (int i = threadIdx.x; i < K * NB; i += blockDim.x) a.Rr[i] = -a.R[i];
+        __syncthreads();
+        if (threadIdx.x < 32) {
+          thomas_factor_f32<NB>(K, a);
+          __syncwarp();
+          thomas_apply_f32<NB>(K, a, a.Rr, a.DX);
+        }
+        __syncthreads();
+        for (int ref = 0; ref < kRefinements; ++ref) {
+          linear_residual_f64<NB>(K, a);
+          __syncthreads();
+          if (threadIdx.x < 32) thomas_apply_f32<NB>(K, a, a.Rr, a.Dx2);
+          __syncthreads();
+          for (int i = threadIdx.x; i < K * NB; i += blockDim.x) a.DX[i] += a.Dx2[i];
+          __syncthreads();
+        }
+      } else {
+        if (threadIdx.x < 32) thomas_warp<NB>(K, a);
+        __syncthreads();
+      }
+    } else {
+      if (threadIdx.x < 32) thomas_warp<NB>(K, a);
+      __syncthreads();
+    }
+    double dm = 0.0, xm = 0.0;
+    for (int i = threadIdx.x; i < K * NB; i += blockDim.x) {
+      const double d = a.DX[i];
+      const double xn = a.X[i] + d;
+      a.X[i] = xn;
+      dm = fmax(dm, fabs(d));
+      xm = fmax(xm, fabs(xn));
+    }
+    dxmax = block_max(dm, sred);
+    xmax = block_max(xm, sred);
+    __syncthreads();
+  }
+  __syncthreads();
+  its_out = its;
+  conv_out = conv;
+  xmax_out = xmax;
+}
+
 template <int P, int M3>
 __global__ void __launch_bounds__(256) implicit_kernel(ImplArgs a, ImplOps<P, M3> o, long long n_steps) {
   using S = IS<P, M3>;
@@ -620,70 +699,20 @@ __global__ void __launch_bounds__(256) implicit_kernel(ImplArgs a, ImplOps<P, M3
       }
     }
     __syncthreads();
-    double r0 = 0.0, dxmax = 0.0, xmax = 0.0;
+    // continuation in gamma (Sec. 6.3): gamma_i = gamma0 + (i-1)(gamma-gamma0)/(n_gamma-1)
+    const int ng = a.n_gamma > 1 ? a.n_gamma : 1;
     int its = 0;
-    bool conv = false;
-    for (int it = 0;; ++it) {
-      double part = 0.0;
-      for (int e = threadIdx.x; e < K; e += blockDim.x) part += assemble<P, M3>(e, a, o);
-      const double rn = sqrt(block_sum(part, sred));
-      if (it == 0) {
-        r0 = rn;
-        if (rn <= a.atol) {
-          conv = true;
-          its = 0;
-          break;
-        }
-      } else if (rn <= a.rtol * r0 || rn <= a.atol || dxmax <= a.xtol * (1.0 + xmax)) {
-        conv = true;
-        its = it;
-        break;
-      }
-      if (it == a.max_it || !(rn == rn)) {
-        its = it;
-        break;
-      }
-      __syncthreads();
-      if constexpr (3 * NB <= 32) {
-        if (a.mixed) {
-          // -R into Rr, FP32 factor + solve, then FP64 residual / correction rounds
-          for (int i = threadIdx.x; i < K * NB; i += blockDim.x) a.Rr[i] = -a.R[i];
-          __syncthreads();
-          if (threadIdx.x < 32) {
-            thomas_factor_f32<NB>(K, a);
-            __syncwarp();
-            thomas_apply_f32<NB>(K, a, a.Rr, a.DX);
-          }
-          __syncthreads();
-          for (int ref = 0; ref < kRefinements; ++ref) {
-            linear_residual_f64<NB>(K, a);
-            __syncthreads();
-            if (threadIdx.x < 32) thomas_apply_f32<NB>(K, a, a.Rr, a.Dx2);
-            __syncthreads();
-            for (int i = threadIdx.x; i < K * NB; i += blockDim.x) a.DX[i] += a.Dx2[i];
-            __syncthreads();
-          }
-        } else {
-          if (threadIdx.x < 32) thomas_warp<NB>(K, a);
-          __syncthreads();
-        }
-      } else {
-        if (threadIdx.x < 32) thomas_warp<NB>(K, a);
-        __syncthreads();
-      }
-      double dm = 0.0, xm = 0.0;
-      for (int i = threadIdx.x; i < K * NB; i += blockDim.x) {
-        const double d = a.DX[i];
-        const double xn = a.X[i] + d;
-        a.X[i] = xn;
-        dm = fmax(dm, fabs(d));
-        xm = fmax(xm, fabs(xn));
-      }
-      dxmax = block_max(dm, sred);
-      xmax = block_max(xm, sred);
-      __syncthreads();
+    bool conv = true;
+    double xmax = 0.0;
+    for (int ic = 0; ic < ng; ++ic) {
+      ImplArgs b = a;
+      if (ng > 1) b.gamma = a.gamma0 + ic * (a.gamma - a.gamma0) / (ng - 1);
+      int it_s;
+      bool cv_s;
+      newton_solve<P, M3>(b, o, sred, it_s, cv_s, xmax);
+      its += it_s;
+      conv = conv && cv_s;
     }
-    __syncthreads();
     if (threadIdx.x == 0) {
       dg_implicit_stats& st = *a.st;
       st.steps += 1;
@@ -697,7 +726,6 @@ __global__ void __launch_bounds__(256) implicit_kernel(ImplArgs a, ImplOps<P, M3
     __syncthreads();
     if (a.st->status != 0) break;
   }
-  // final residual norm of the last step is recomputed on the host side if needed
 }
 
 // E consistent with V (R_E = 0; element-local solve of <N_E, N_E> E = rhs),
@@ -848,6 +876,8 @@ ImplArgs make_args(dg_implicit* s) {
   a.max_it = s->ip.max_it;
   a.on_fail_continue = s->ip.on_fail_continue;
   a.mixed = s->ip.linear_solver == 1 ? 1 : 0;
+  a.n_gamma = s->ip.n_gamma;
+  a.gamma0 = s->ip.gamma0;
   a.Wf = s->at<float>(s->off.Wf);
   a.Af = s->at<float>(s->off.Af);
   a.Rr = s->at<double>(s->off.Rr);
@@ -956,6 +986,10 @@ dg_status dg_implicit_init(const dg_swe_mesh* mesh, int order, int regularizatio
   if (!(ip->dt > 0) || ip->max_it < 1 || m3 < 0 || m3 > order || ip->linear_solver < 0 || ip->linear_solver > 1) {
     *out = s.release();
     return ifail(*out, DG_ERR_ARG, "need dt > 0, max_it >= 1, 0 <= m3 <= order, linear_solver in {0, 1}");
+  }
+  if (ip->n_gamma > 1 && !(ip->gamma0 > 0)) {
+    *out = s.release();
+    return ifail(*out, DG_ERR_ARG, "continuation needs gamma0 > 0");
   }
   if (ip->linear_solver == 1 && 3 * (2 * (order + 1) + m3 + 1) > 32) {
     *out = s.release();

@@ -146,3 +146,42 @@ def test_mixed_precision_solve_yield_and_p2():
     d, im, X, Vo, its_o = _oracle_run(c2, 2e-4, 5)
     s, V, its_g = _gpu_mixed(c2, 2e-4, 5)
     assert rel_l2(V, Vo) < 1e-11
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_gamma_continuation_matches_oracle(mixed):
+    """Continuation gamma0 = 1e2 -> gamma = 1e3 in two stages per step
+    (Sec. 6.3, Table damBreakContinuation setup): iteration counts (summed over
+    stages) and states match the oracle."""
+    import paper_2301_11238_gb300 as G
+    c = synth.paper_dam_break_1d(n_el=100, order=1, m3=0, reg=1, gamma=1e3, beta=1e3)
+    d, V0, _ = build(c)
+    im = Implicit1D(d, 1e-6)
+    Vh0 = d.to_modal(V0)
+    X = im.pack(Vh0, im.initial_E(Vh0))
+    its_o = []
+    for _ in range(15):
+        X, it, ok = im.step_continuation(X, 2, 1e2)
+        its_o.append(it)
+        assert ok
+    Vo = d.to_nodal(im.unpack(X)[0])
+    s, _ = G.implicit_from_case(c, dt=1e-6, n_gamma=2, gamma0=1e2, mixed=mixed)
+    its_g = [s.run(1)["last_its"] for _ in range(15)]
+    V, _ = s.get_state()
+    assert all(abs(a - b) <= 1 for a, b in zip(its_g, its_o))
+    assert rel_l2(V, Vo) < 1e-12
+
+
+def test_paper_dam_break_active_region_table_damBreakFuns():
+    """The paper's dam break run to t = 0.15 s (150,000 backward-Euler steps
+    of 1e-6 s on 100 elements, regularization 1 with gamma = beta = 1e2):
+    the active region and Newton iterations per step of Table damBreakFuns
+    (about three minutes on the GPU)."""
+    import paper_2301_11238_gb300 as G
+    gold = GOLD["dam_break_active_percent_n100"]
+    c = synth.paper_dam_break_1d(n_el=100, order=1, m3=0, reg=1, gamma=1e2, beta=1e2)
+    s, _ = G.implicit_from_case(c, dt=1e-6, mixed=True)
+    st = s.run(150000)
+    assert st["failed_steps"] == 0 and abs(st["t"] - 0.15) < 1e-9
+    assert abs(s.active_percent() - gold["reg1_gamma1e2_beta1e2"]) <= 1.0
+    assert abs(st["newton_its"] / st["steps"] - gold["nr_its_per_step"]) < 0.5

@@ -143,3 +143,19 @@ def test_implicit_mass_conservation_walls():
     Vh, _ = im.unpack(X)
     assert fails == 0
     assert abs(d.total_mass(Vh) - m0) < 1e-12 * m0
+
+
+def test_gamma_continuation_converges_to_final_gamma():
+    """Continuation (Sec. 6.3) ends each step at the target gamma: one step
+    with gamma0 -> gamma equals a plain step at gamma to the Newton
+    tolerance, and takes at least as many iterations in total."""
+    c = synth.paper_dam_break_1d(n_el=40, order=1, m3=0, reg=1, gamma=1e3, beta=1e3)
+    d, V0, _ = build(c)
+    im = Implicit1D(d, 1e-6)
+    Vh0 = d.to_modal(V0)
+    X0 = im.pack(Vh0, im.initial_E(Vh0))
+    Xa, ita, oka = im.step(X0)
+    Xb, itb, okb = im.step_continuation(X0, 3, 1e2)
+    assert oka and okb and itb >= ita
+    assert np.abs(Xa - Xb).max() < 1e-9 * np.abs(Xa).max()
+    assert im.prm["gamma"] == 1e3  # restored after the stages
