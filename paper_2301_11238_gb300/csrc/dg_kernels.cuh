@@ -96,6 +96,27 @@ struct DevScalars {
   int pad;
 };
 
+// ------------------------------------------------------------------ arithmetic helpers
+// FP64 keeps IEEE division and square root.  FP32 uses the fast hardware
+// forms (division, reciprocal square root and square root within 2 ulp),
+// well inside the FP32 path's stated tolerance.
+template <typename R>
+__device__ __forceinline__ R dg_div(R a, R b) { return a / b; }
+template <>
+__device__ __forceinline__ float dg_div<float>(float a, float b) { return __fdividef(a, b); }
+template <typename R>
+__device__ __forceinline__ R dg_rsqrt(R x) { return R(1) / sqrt(x); }
+template <>
+__device__ __forceinline__ float dg_rsqrt<float>(float x) { return rsqrtf(x); }
+template <typename R>
+__device__ __forceinline__ R dg_sqrt(R x) { return sqrt(x); }
+template <>
+__device__ __forceinline__ float dg_sqrt<float>(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // ------------------------------------------------------------------ physics
 
 // phi_k(s) / (2 s) for s >= 0 (limit phi_k'(0)/2 at s = 0): the Bingham
@@ -109,29 +130,29 @@ __device__ __forceinline__ R bingham_coef(R s, const Phys<R>& ph) {
       R e = R(0.5) / ph.beta;
       R x = g * s - s0;
       R mb = x >= e ? x : (x <= -e ? R(0) : R(0.5) * ph.beta * (x + e) * (x + e));
-      return s0 * g / (mb + s0);
+      return dg_div<R>(s0 * g, mb + s0);
     }
     case 2: {  // local quadratic, Eq. sigmaTwoB
       R e = R(0.5) / ph.beta;
       R x = g * s;
-      if (x >= s0 + e) return s0 / s;
+      if (x >= s0 + e) return dg_div<R>(s0, s);
       if (x <= s0 - e) return g;
       R d = s0 - x + e;
-      return (R(2) * s0 - ph.beta * d * d) / (R(2) * s);
+      return dg_div<R>(R(2) * s0 - ph.beta * d * d, R(2) * s);
     }
     case 3: {  // tanh, Eq. sigmaTwoC
       R x = g * s;
       if (x < R(1e-8)) return s0 * g * (R(1) - x * x / R(3));
-      return s0 * tanh(x) / s;
+      return dg_div<R>(s0 * tanh(x), s);
     }
     case 4: {  // exponential (extension)
       R x = ph.pap_m * s;
       if (x < R(1e-12)) return s0 * ph.pap_m * (R(1) - R(0.5) * x);
-      return -s0 * expm1(-x) / s;
+      return dg_div<R>(-s0 * expm1(-x), s);
     }
     case 5: {  // bi-viscosity (extension)
       R x = g * s;
-      return x < s0 ? g : s0 / s;
+      return x < s0 ? g : dg_div<R>(s0, s);
     }
   }
   return R(0);
@@ -148,7 +169,7 @@ __device__ __forceinline__ void stress(const R* E, const Phys<R>& ph, R sig[DIM]
     R d11 = E[0], d22 = E[3], d12 = R(0.5) * (E[1] + E[2]);
     R tr = d11 + d22;
     R nc2 = d11 * d11 + R(2) * d12 * d12 + d22 * d22 + tr * tr;
-    R s = sqrt(R(0.5) * nc2);
+    R s = dg_sqrt<R>(R(0.5) * nc2);
     R mu = R(2) * ph.eta + bingham_coef<R>(s, ph);
     sig[0][0] = mu * (d11 + tr);
     sig[1][1] = mu * (d22 + tr);
@@ -196,8 +217,8 @@ __device__ __forceinline__ void hll(const R* Vm, const R* Vp, const R* n, const 
     unm += Vm[1 + j] * n[j];
     unp += Vp[1 + j] * n[j];
   }
-  R cm = sqrt(ph.gc * fmax(hm, ph.h_floor));
-  R cp = sqrt(ph.gc * fmax(hp, ph.h_floor));
+  R cm = dg_sqrt<R>(ph.gc * fmax(hm, ph.h_floor));
+  R cp = dg_sqrt<R>(ph.gc * fmax(hp, ph.h_floor));
   R SL = fmin(unm - cm, unp - cp);
   R SR = fmax(unm + cm, unp + cp);
   R Fm[DIM + 1], Fp[DIM + 1];
@@ -216,7 +237,7 @@ __device__ __forceinline__ void hll(const R* Vm, const R* Vp, const R* n, const 
 #pragma unroll
     for (int v = 0; v < DIM + 1; ++v) Fn[v] = Fp[v];
   } else {
-    R inv = R(1) / (SR - SL);
+    R inv = dg_div<R>(R(1), SR - SL);
     R Um[DIM + 1], Up[DIM + 1];
     Um[0] = hm;
     Up[0] = hp;
@@ -271,7 +292,7 @@ __global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__
     G[1][0] = geo[2 * K + e];
     G[1][1] = geo[3 * K + e];
   }
-  const R Jinv = R(1) / geo[4 * K + e];
+  const R Jinv = dg_div<R>(R(1), geo[4 * K + e]);
   R Eo[NE][NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
@@ -595,7 +616,7 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
   }
 
   // ---- mass solve: M dh/dt = -r_h ; M_h du/dt = -r_u - M_u dh/dt
-  const R Jinv = R(1) / J;
+  const R Jinv = dg_div<R>(R(1), J);
   R dV[NV][NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
@@ -655,7 +676,7 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
     R d = Mh[a][a];
 #pragma unroll
     for (int c = 0; c < a; ++c) d -= Mh[a][c] * Mh[a][c];
-    dinv[a] = R(1) / sqrt(d);
+    dinv[a] = dg_rsqrt<R>(d);
   }
 #pragma unroll
   for (int j = 0; j < DIM; ++j) {
