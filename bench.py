@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--mode", default="batch", choices=["batch", "solo"],
                     help="batch: all instances in one dg_batch (one launch per phase); solo: one context each")
     ap.add_argument("--inner", type=int, default=None, help="RK3 steps per instance per bench step")
-    ap.add_argument("--n", type=int, default=None, help="squares per side (radial workload)")
+    ap.add_argument("--n", type=int, default=None,
+                    help="squares per side of the 2D mesh (radial 64, bump 512, slump 2048); "
+                         "smaller values give profiling cases of the same kernels")
     ap.add_argument("--order", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -64,7 +66,7 @@ def parse():
     if a.inner is None:
         a.inner = d["inner"]
     if a.n is None:
-        a.n = 64
+        a.n = {"bump": 512, "slump": 2048}.get(a.workload, 64)
     return a
 
 
@@ -95,12 +97,12 @@ def workload_cases(args):
     if args.workload == "dam1d":
         return [synth.dam_break_1d()]
     if args.workload == "bump":
-        return [synth.bump_dam_2d()]
+        return [synth.bump_dam_2d(n=args.n)]
     if args.workload == "ensemble":
         return synth.ensemble_cases()
     if args.workload == "implicit_dam":
         return [synth.paper_dam_break_1d(n_el=100, order=1, m3=0, reg=1, gamma=1e2, beta=1e2)]
-    return [synth.slump_2d()]
+    return [synth.slump_2d(n=args.n)]
 
 
 def sample_case(workload, n, order):
@@ -128,9 +130,9 @@ def workload_name(args):
         return (f"radial_dam_2d {args.n}x{args.n}x2 triangles on [-1,1]^2, p={args.order}, "
                 f"sigma0 in {list(SIGMAS)} x regularization in {list(REGS)} (gamma=beta=1e3, eta=0.01)")
     return {"dam1d": "dam_break_1d 200 elements on [0,1], p=1, exponential regularization m=1e3, sigma0=0.05",
-            "bump": "bump_dam_2d 512x512x2 jittered triangles (seed 3), p=3, tanh regularization gamma=1e3",
+            "bump": f"bump_dam_2d {args.n}x{args.n}x2 jittered triangles (seed 3), p=3, tanh regularization gamma=1e3",
             "ensemble": "ensemble of 256 instances (seed 4): 1D/2D, p in {1,2,3}, 1e3..5e4 elements",
-            "slump": "slump_2d 2048x2048x2 triangles, p=2, slope 0.05, 16-mode bed (seed 5), bi-viscosity",
+            "slump": f"slump_2d {args.n}x{args.n}x2 triangles, p=2, slope 0.05, 16-mode bed (seed 5), bi-viscosity",
             "implicit_dam": "paper_dam_break_1d 100 elements, p=1, m3=0, backward Euler + Newton, dt=1e-6, "
                             "regularization 1 gamma=beta=1e2"}[
         args.workload]

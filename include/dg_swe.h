@@ -49,7 +49,9 @@ typedef enum {
   DG_ERR_WORKSPACE = 3,    /* workspace missing, too small or misaligned      */
   DG_ERR_NONFINITE = 4,    /* the state became NaN/Inf (latched on device)    */
   DG_ERR_NEWTON = 5,       /* Newton did not converge (implicit integrator)   */
-  DG_ERR_UNSUPPORTED = 6   /* feature not available for this configuration    */
+  DG_ERR_UNSUPPORTED = 6,  /* feature not available for this configuration    */
+  DG_ERR_TIMEOUT = 7       /* a bounded in-kernel wait ran out (latched on
+                              device; the step's results are not valid)      */
 } dg_status;
 
 typedef struct dg_swe_ctx dg_swe_ctx;

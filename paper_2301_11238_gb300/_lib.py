@@ -4,9 +4,10 @@ import os
 
 from . import build as _build
 
-DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_WORKSPACE, DG_ERR_NONFINITE, DG_ERR_NEWTON, DG_ERR_UNSUPPORTED = range(7)
+(DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_WORKSPACE, DG_ERR_NONFINITE, DG_ERR_NEWTON, DG_ERR_UNSUPPORTED,
+ DG_ERR_TIMEOUT) = range(8)
 STATUS_NAMES = {0: "DG_OK", 1: "DG_ERR_ARG", 2: "DG_ERR_CUDA", 3: "DG_ERR_WORKSPACE",
-                4: "DG_ERR_NONFINITE", 5: "DG_ERR_NEWTON", 6: "DG_ERR_UNSUPPORTED"}
+                4: "DG_ERR_NONFINITE", 5: "DG_ERR_NEWTON", 6: "DG_ERR_UNSUPPORTED", 7: "DG_ERR_TIMEOUT"}
 MAX_BC = 8
 
 

@@ -27,6 +27,8 @@ struct GroupDrv {
   virtual void estep(dg_batch* b, Group& g, int vin, cudaStream_t s) = 0;
   virtual void face(dg_batch* b, Group& g, int vin, cudaStream_t s) = 0;
   virtual void volume(dg_batch* b, Group& g, int vin, int vout, double c0, double c1, cudaStream_t s) = 0;
+  // whether a volume block size is launchable (negative: staged form)
+  virtual bool volume_ok(int tile) = 0;
   virtual void dt(dg_batch* b, Group& g, cudaStream_t s) = 0;
   virtual void mass(dg_batch* b, Group& g, int first, int count, int set_ref, cudaStream_t s) = 0;
 };
@@ -99,7 +101,40 @@ struct GDrv final : GroupDrv {
   EstepOps<DIM, P, R> eo{};
   FaceOps<DIM, P, R> fo{};
   VolOps<DIM, P, R> vo{};
-  explicit GDrv(const RefOps& o) { fill_ops<DIM, P, R>(o, eo, fo, vo); }
+  int n_sm = 0;
+  size_t smem_optin = 0;
+  std::map<int, int> staged_grid;  // staged volume block size -> persistent grid size (0: not launchable)
+  explicit GDrv(const RefOps& o) {
+    fill_ops<DIM, P, R>(o, eo, fo, vo);
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) {
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) n_sm = v;
+      if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
+        smem_optin = (size_t)v;
+    }
+    if (smem_optin)
+      cudaFuncSetAttribute(volume_staged_kernel<DIM, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)smem_optin);
+    cudaGetLastError();
+  }
+  // persistent grid of the staged volume kernel: resident blocks per SM x SMs
+  int staged_blocks(int T) {
+    auto it = staged_grid.find(T);
+    if (it != staged_grid.end()) return it->second;
+    int nb = 0;
+    const size_t smem = staged_smem_bytes<DIM, P, R>(T);
+    if (n_sm > 0 && smem <= smem_optin &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, volume_staged_kernel<DIM, P, R>, T, smem) != cudaSuccess)
+      nb = 0;
+    cudaGetLastError();
+    staged_grid[T] = nb * n_sm;
+    return nb * n_sm;
+  }
+  bool volume_ok(int tile) override {
+    if (tile > 0) return tile >= 32 && tile <= 256 && tile % 32 == 0;
+    const int T = -tile;
+    return T >= 32 && T <= 256 && T % 32 == 0 && staged_blocks(T) > 0;
+  }
 
   const Phys<R>* ptab(dg_batch* b) { return b->at<Phys<R>>(b->off_ptab); }
   const BCEntry<R>* bct(dg_batch* b) { return b->at<BCEntry<R>>(b->off_bct); }
@@ -127,7 +162,20 @@ struct GDrv final : GroupDrv {
     }
   }
   void volume(dg_batch* b, Group& g, int vin, int vout, double c0, double c1, cudaStream_t s) override {
-    const int K = (int)g.K, F = (int)g.F, T = g.tile[2];
+    const int K = (int)g.K, F = (int)g.F;
+    if (g.tile[2] < 0) {
+      const int T = -g.tile[2];
+      const int ntiles = (K + T - 1) / T;
+      const int grid = std::min(ntiles, staged_blocks(T));
+      if (grid <= 0) return;
+      volume_staged_kernel<DIM, P, R><<<grid, T, staged_smem_bytes<DIM, P, R>(T), s>>>(
+          K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.V[0]), b->at<R>(g.off.V[vout]), b->at<R>(g.off.E),
+          g.has_bed ? b->at<R>(g.off.bed) : nullptr, b->at<R>(g.off.geo), b->at<int32_t>(g.off.fid),
+          b->at<R>(g.off.wflux), vo, ptab(b), b->at<int32_t>(g.off.inst), (R)c0, (R)c1,
+          b->at<DevScalars>(b->off_sc));
+      return;
+    }
+    const int T = g.tile[2];
     volume_kernel<DIM, P, R, true><<<(K + T - 1) / T, T, 0, s>>>(
         K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.V[0]), b->at<R>(g.off.V[vout]), b->at<R>(g.off.E),
         g.has_bed ? b->at<R>(g.off.bed) : nullptr, b->at<R>(g.off.geo), b->at<int32_t>(g.off.fid),
@@ -246,7 +294,11 @@ dg_status read_stats(dg_batch* b, dg_swe_stats* st) {
     st[i].mass0 = h[i].mass0;
     st[i].status = h[i].status;
   }
-  if (bad >= 0) return bfail(b, (dg_status)h[bad].status, "device status: non-finite state in instance " + std::to_string(bad));
+  if (bad >= 0)
+    return bfail(b, (dg_status)h[bad].status,
+                 std::string(h[bad].status == DG_ERR_TIMEOUT ? "device status: staged copy wait timed out"
+                                                              : "device status: non-finite state") +
+                     " in instance " + std::to_string(bad));
   return DG_OK;
 }
 
@@ -647,8 +699,10 @@ dg_status dg_batch_autotune(dg_batch* b, int n_iter) {
     for (int k = 0; k < 3; ++k) {
       float best = 1e30f;
       int best_t = g.tile[k];
-      const int ncand = k == 1 ? 8 : 4;  // the face kernel also tries its per-face form
+      // the face kernel also tries its per-face form, the volume kernel its staged form
+      const int ncand = k == 0 ? 4 : 8;
       for (int ci = 0; ci < ncand; ++ci) {
+        if (k == 2 && !g.drv->volume_ok(cand[ci])) continue;
         g.tile[k] = cand[ci];
         auto launch = [&]() {
           if (k == 0) g.drv->estep(b, g, 0, s);
@@ -729,8 +783,14 @@ dg_status dg_batch_tiles(const dg_batch* b, int32_t* out, int cap, int32_t* n_gr
 dg_status dg_batch_set_tiles(dg_batch* b, const int32_t* tiles, int n) {
   if (!b || !tiles || n != 3 * (int)b->groups.size()) return bfail(b, DG_ERR_ARG, "need 3 block sizes per group");
   for (int i = 0; i < n; ++i) {
-    const int v = (i % 3 == 1 && tiles[i] < 0) ? -tiles[i] : tiles[i];
-    if (v < 32 || v > 256 || v % 32) return bfail(b, DG_ERR_ARG, "block sizes must be 32..256, multiples of 32 (negative face entry: per-face form)");
+    const int v = (i % 3 != 0 && tiles[i] < 0) ? -tiles[i] : tiles[i];
+    if (v < 32 || v > 256 || v % 32)
+      return bfail(b, DG_ERR_ARG,
+                   "block sizes must be 32..256, multiples of 32 (negative face entry: per-face form; negative "
+                   "volume entry: staged form)");
+    if (i % 3 == 2 && !b->groups[i / 3].drv->volume_ok(tiles[i]))
+      return bfail(b, DG_ERR_ARG, "staged volume block size " + std::to_string(-tiles[i]) +
+                                      " does not fit in shared memory for this group");
   }
   for (size_t g = 0; g < b->groups.size(); ++g)
     for (int k = 0; k < 3; ++k) b->groups[g].tile[k] = tiles[3 * g + k];

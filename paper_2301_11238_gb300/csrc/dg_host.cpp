@@ -240,24 +240,14 @@ bool build_refops(int dim, int p, RefOps& o, std::string& err) {
   }
   // faces
   o.fmask.assign(o.nf * o.Nfp, 0);
+  for (int f = 0; f < o.nf; ++f)
+    for (int k = 0; k < o.Nfp; ++k) o.fmask[f * o.Nfp + k] = face_node(dim, p, f, k);
   if (dim == 1) {
-    o.fmask[0] = 0;
-    o.fmask[1] = p;
     o.Nfq = 1;
     o.tf = {0.0};
     o.wf = {1.0};
     o.Lf = {1.0};
   } else {
-    auto idx = [&](int i, int j) {
-      int base = 0;
-      for (int jj = 0; jj < j; ++jj) base += p + 1 - jj;
-      return base + i;
-    };
-    for (int k = 0; k <= p; ++k) {
-      o.fmask[0 * o.Nfp + k] = idx(k, 0);
-      o.fmask[1 * o.Nfp + k] = idx(p - k, k);
-      o.fmask[2 * o.Nfp + k] = idx(0, p - k);
-    }
     gauss_jacobi(nfq, 0.0, 0.0, o.tf, o.wf);
     o.Nfq = nfq;
     o.Lf.assign(nfq * o.Nfp, 0);

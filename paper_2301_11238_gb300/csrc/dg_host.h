@@ -12,7 +12,37 @@
 #include <string>
 #include <vector>
 
+#if defined(__CUDACC__)
+#define DG_HOST_DEVICE __host__ __device__
+#else
+#define DG_HOST_DEVICE
+#endif
+
 namespace dgswe {
+
+// Element-local index of node k of face f in the equispaced nodal ordering.
+// 1D: nodes 0..p from left to right; face 0 is the left end, face 1 the
+// right.  Triangles: node (i, j), i + j <= p, has index
+// sum_{jj < j} (p + 1 - jj) + i; face 0 is j = 0, face 1 is i + j = p and
+// face 2 is i = 0, each walked counter-clockwise.  The kernels evaluate it
+// with compile-time arguments, so the node indices become constants.
+DG_HOST_DEVICE constexpr int face_node(int dim, int p, int f, int k) {
+  if (dim == 1) return f == 0 ? 0 : p;
+  int i = 0, j = 0;
+  if (f == 0) {
+    i = k;
+    j = 0;
+  } else if (f == 1) {
+    i = p - k;
+    j = k;
+  } else {
+    i = 0;
+    j = p - k;
+  }
+  int base = 0;
+  for (int jj = 0; jj < j; ++jj) base += p + 1 - jj;
+  return base + i;
+}
 
 // Gauss-Jacobi rule for weight (1-x)^a (1+x)^b on [-1,1] by Golub-Welsch.
 void gauss_jacobi(int n, double a, double b, std::vector<double>& x, std::vector<double>& w);

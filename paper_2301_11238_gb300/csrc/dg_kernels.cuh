@@ -86,7 +86,6 @@ struct VolOps {
   R wq[S::NQ];
   R Minv[S::NP * S::NP];
   R LfT[S::NFP * S::NFQ];  // Lf transposed: lift of face-point values to face nodes
-  int8_t fmask[S::NF * S::NFP];
 };
 
 struct DevScalars {
@@ -324,7 +323,7 @@ __global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__
       const int f2 = nbrf[f * K + e];
 #pragma unroll
       for (int k = 0; k < NFP; ++k) {
-        const int a = ops.fmask[f * NFP + k];
+        const int a = face_node(DIM, P, f, k);
         const int b = ops.fmask[f2 * NFP + (NFP - 1 - k)];
 #pragma unroll
         for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (V[(1 + j) * KN + (size_t)e2 * NP + b] - u[j][a]);
@@ -333,7 +332,7 @@ __global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__
       const BCEntry<R> bc = bct[-1 - e2];
 #pragma unroll
       for (int k = 0; k < NFP; ++k) {
-        const int a = ops.fmask[f * NFP + k];
+        const int a = face_node(DIM, P, f, k);
         R Vm[DIM + 1], Vp[DIM + 1];
         Vm[0] = R(1);
 #pragma unroll
@@ -471,22 +470,23 @@ __global__ void __launch_bounds__(256) face_kernel(int K, int F, const R* __rest
   }
 }
 
-// mode 0: write dV/dt to out; mode 1: out = c0 * V0 + c1 * (Vin + dt * dV/dt).
-template <int DIM, int P, typename R, bool BATCH>
-__global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __restrict__ Vin,
-                                                     const R* V0, R* out,
-                                                     const R* __restrict__ E, const R* __restrict__ bed,
-                                                     const R* __restrict__ geo, const int32_t* __restrict__ fid,
-                                                     const R* __restrict__ wflux, const VolOps<DIM, P, R> ops,
-                                                     const Phys<R> ph0, const Phys<R>* __restrict__ ptab,
-                                                     const int32_t* __restrict__ inst, int mode, R c0, R c1,
-                                                     const DevScalars* __restrict__ sc) {
+// Everything the volume kernels do for one element e once its nodal values
+// are in registers: volume integrals, face lift, mass solve and output.
+// bed_e: the element's NP bed values (nullptr: flat bed).  V0e[v]: the
+// element's values of field v of the stage's first state (read in mode 1
+// when c0 != 0).  mode 0: write dV/dt to out; mode 1: out = c0 * V0 + c1 * (Vin +
+// dt * dV/dt).
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                               const R (&En)[Sh<DIM, P>::NE][Sh<DIM, P>::NP],
+                                               const R* __restrict__ bed_e, const R* const (&V0e)[Sh<DIM, P>::NV],
+                                               R* out,
+                                               const R* __restrict__ geo, const int32_t* __restrict__ fid,
+                                               const R* __restrict__ wflux, const VolOps<DIM, P, R>& ops,
+                                               const Phys<R>& ph, int ins, int mode, R c0, R c1,
+                                               const DevScalars* __restrict__ sc) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NQ = S::NQ, NF = S::NF, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV, NE = S::NE;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= K) return;
-  const int ins = BATCH ? inst[e] : 0;
-  const Phys<R> ph = BATCH ? ptab[ins] : ph0;
   const size_t KN = (size_t)K * NP;
   const size_t eo = (size_t)e * NP;
   R G[2][2];
@@ -502,15 +502,6 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
   for (int v = 0; v < NV; ++v)
 #pragma unroll
     for (int a = 0; a < NP; ++a) r[v][a] = R(0);
-  // the element's nodal values, read once (each is used at every volume point)
-  R Vn[NV][NP], En[NE][NP];
-#pragma unroll
-  for (int a = 0; a < NP; ++a) {
-#pragma unroll
-    for (int v = 0; v < NV; ++v) Vn[v][a] = Vin[v * KN + eo + a];
-#pragma unroll
-    for (int c = 0; c < NE; ++c) En[c][a] = E[c * KN + eo + a];
-  }
 
   // ---- volume integrals: -<grad N, F - Q> - <N, S>  (Eq. WeakForm51)
 #pragma unroll 1
@@ -528,8 +519,8 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
       for (int v = 0; v < NV; ++v) Vq[v] += l * Vn[v][a];
 #pragma unroll
       for (int c = 0; c < NE; ++c) Eq[c] += l * En[c][a];
-      if (bed) {
-        const R H = bed[eo + a];
+      if (bed_e) {
+        const R H = bed_e[a];
         Hr += ops.Drq[q * NP + a] * H;
         if constexpr (DIM == 2) Hs += ops.Dsq[q * NP + a] * H;
       }
@@ -604,7 +595,7 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
       }
 #pragma unroll
     for (int k = 0; k < NFP; ++k) {
-      const int a = ops.fmask[f * NFP + k];
+      const int a = face_node(DIM, P, f, k);
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
         R acc = R(0);
@@ -711,9 +702,232 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
       for (int a = 0; a < NP; ++a) {
         const R vi = Vn[v][a];
         R y = c1 * (vi + dt * dV[v][a]);
-        if (c0 != R(0)) y += c0 * V0[v * KN + eo + a];
+        if (c0 != R(0)) y += c0 * V0e[v][a];
         out[v * KN + eo + a] = y;
       }
+  }
+}
+
+// One thread per element; nodal values read straight from global memory.
+template <int DIM, int P, typename R, bool BATCH>
+__global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __restrict__ Vin,
+                                                     const R* V0, R* out,
+                                                     const R* __restrict__ E, const R* __restrict__ bed,
+                                                     const R* __restrict__ geo, const int32_t* __restrict__ fid,
+                                                     const R* __restrict__ wflux, const VolOps<DIM, P, R> ops,
+                                                     const Phys<R> ph0, const Phys<R>* __restrict__ ptab,
+                                                     const int32_t* __restrict__ inst, int mode, R c0, R c1,
+                                                     const DevScalars* __restrict__ sc) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NV = S::NV, NE = S::NE;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  const int ins = BATCH ? inst[e] : 0;
+  const Phys<R> ph = BATCH ? ptab[ins] : ph0;
+  const size_t KN = (size_t)K * NP;
+  const size_t eo = (size_t)e * NP;
+  // the element's nodal values, read once (each is used at every volume point)
+  R Vn[NV][NP], En[NE][NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Vn[v][a] = Vin[v * KN + eo + a];
+#pragma unroll
+    for (int c = 0; c < NE; ++c) En[c][a] = E[c * KN + eo + a];
+  }
+  const R* V0e[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) V0e[v] = V0 ? V0 + v * KN + eo : nullptr;
+  volume_element<DIM, P, R>(e, K, F, Vn, En, bed ? bed + eo : nullptr, V0e, out, geo, fid, wflux, ops, ph, ins, mode,
+                            c0, c1, sc);
+}
+
+// ------------------------------------------------------------------ staged volume kernel
+// Bulk asynchronous copies (global -> shared, completion counted in bytes on
+// an mbarrier) and a bounded mbarrier wait.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase of the given parity to complete; false after
+// limit_ns nanoseconds without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  while (!mbar_test(bar, parity))
+    if (global_ns() - t0 > limit_ns) return false;
+  return true;
+}
+
+constexpr uint64_t kStageWaitNs = 1000000000ull;  // 1 s: copies of a few KB take microseconds
+
+// Bytes of one staging slot: a tile's contiguous range of one field plus the
+// up-to-15-byte lead of its 16-byte aligned window, rounded up to 16.
+template <typename R>
+__host__ __device__ constexpr uint32_t staged_slot_bytes(int T, int NP) {
+  return (uint32_t)(((size_t)T * NP * sizeof(R) + 16 + 15) & ~size_t(15));
+}
+// Staged arrays per buffer: V (NV fields), E (NE), bed, V0 (NV).
+template <int DIM, int P>
+__host__ __device__ constexpr int staged_arrays() {
+  return 2 * Sh<DIM, P>::NV + Sh<DIM, P>::NE + 1;
+}
+template <int DIM, int P, typename R>
+__host__ __device__ constexpr size_t staged_smem_bytes(int T) {
+  return 2 * (size_t)staged_arrays<DIM, P>() * staged_slot_bytes<R>(T, Sh<DIM, P>::NP) + 2 * sizeof(uint64_t);
+}
+
+// Staged form of volume_kernel for batch groups (same arithmetic, bitwise
+// equal results).  A persistent grid walks tiles of T = blockDim.x
+// consecutive elements.  While a tile is computed, the element-major nodal
+// arrays of the CTA's next tile -- V, E, the bed and (stages with c0 != 0)
+// V0, each a contiguous range per field -- arrive in the other of two
+// shared-memory buffers by bulk asynchronous copies, one thread issuing them
+// and an mbarrier per buffer counting the bytes.  Each copy covers the
+// 16-byte aligned window around the range (workspace arrays are 256-byte
+// aligned and padded, so the window stays inside the allocation); readers
+// skip the lead.  A wait that exceeds one second latches DG_ERR_TIMEOUT in
+// the instance's status, waits (bounded) for the copies in flight and ends
+// the CTA.
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(256) volume_staged_kernel(int K, int F, const R* __restrict__ Vin, const R* V0,
+                                                            R* out, const R* __restrict__ E,
+                                                            const R* __restrict__ bed, const R* __restrict__ geo,
+                                                            const int32_t* __restrict__ fid,
+                                                            const R* __restrict__ wflux, const VolOps<DIM, P, R> ops,
+                                                            const Phys<R>* __restrict__ ptab,
+                                                            const int32_t* __restrict__ inst, R c0, R c1,
+                                                            DevScalars* sc) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NV = S::NV, NE = S::NE;
+  constexpr int NARR = staged_arrays<DIM, P>();
+  extern __shared__ __align__(128) unsigned char dsm[];
+  const int T = blockDim.x;
+  const uint32_t slot = staged_slot_bytes<R>(T, NP);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dsm + 2 * (size_t)NARR * slot);
+  const size_t KN = (size_t)K * NP;
+  const int ntiles = (K + T - 1) / T;
+  const bool need_v0 = c0 != R(0);
+  // start of field j's range for a tile starting at element e0 (nullptr: not staged)
+  auto src_of = [&](int j, int e0) -> const char* {
+    const R* base;
+    if (j < NV) base = Vin + j * KN;
+    else if (j < NV + NE) base = E + (j - NV) * KN;
+    else if (j == NV + NE) base = bed;
+    else base = need_v0 ? V0 + (j - NV - NE - 1) * KN : nullptr;
+    return base ? reinterpret_cast<const char*>(base + (size_t)e0 * NP) : nullptr;
+  };
+  auto issue = [&](int tile, int buf) {
+    const int e0 = tile * T;
+    const size_t len = (size_t)min(T, K - e0) * NP * sizeof(R);
+    uint32_t total = 0;
+#pragma unroll 1
+    for (int j = 0; j < NARR; ++j) {
+      const char* p = src_of(j, e0);
+      if (!p) continue;
+      const uintptr_t lead = (uintptr_t)p & 15u;
+      total += (uint32_t)((lead + len + 15) & ~size_t(15));
+    }
+    mbar_expect_tx(&bar[buf], total);
+#pragma unroll 1
+    for (int j = 0; j < NARR; ++j) {
+      const char* p = src_of(j, e0);
+      if (!p) continue;
+      const uintptr_t lead = (uintptr_t)p & 15u;
+      bulk_copy_g2s(dsm + ((size_t)buf * NARR + j) * slot, p - lead, (uint32_t)((lead + len + 15) & ~size_t(15)),
+                    &bar[buf]);
+    }
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  // bit b of parity: phase parity to wait for on buffer b; bit b of pending:
+  // copies issued into buffer b and not yet waited for
+  int tile = blockIdx.x, buf = 0;
+  uint32_t parity = 0u, pending = 0u;
+  if (tile < ntiles) {
+    if (threadIdx.x == 0) issue(tile, 0);
+    pending = 1u;
+  }
+  for (; tile < ntiles; tile += gridDim.x) {
+    const int next = tile + gridDim.x;
+    if (next < ntiles) {
+      if (threadIdx.x == 0) issue(next, buf ^ 1);
+      pending |= 1u << (buf ^ 1);
+    }
+    const bool ok = mbar_wait_bounded(&bar[buf], (parity >> buf) & 1u, kStageWaitNs);
+    if (!__syncthreads_and(ok)) {
+      if (threadIdx.x == 0) {
+        atomicExch(&sc[inst[tile * T]].status, (int)DG_ERR_TIMEOUT);
+        for (int b2 = 0; b2 < 2; ++b2)
+          if ((pending >> b2) & 1u) mbar_wait_bounded(&bar[b2], (parity >> b2) & 1u, kStageWaitNs);
+      }
+      __syncthreads();
+      return;
+    }
+    pending &= ~(1u << buf);
+    parity ^= 1u << buf;
+    const int e0 = tile * T;
+    const int e = e0 + threadIdx.x;
+    if (e < K) {
+      const int ins = inst[e];
+      const Phys<R> ph = ptab[ins];
+      const R* sV[NARR];
+#pragma unroll
+      for (int j = 0; j < NARR; ++j) {
+        const char* p = src_of(j, e0);
+        const uintptr_t lead = p ? ((uintptr_t)p & 15u) : 0;
+        sV[j] = reinterpret_cast<const R*>(dsm + ((size_t)buf * NARR + j) * slot + lead) +
+                (size_t)threadIdx.x * NP;
+      }
+      R Vn[NV][NP], En[NE][NP];
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) Vn[v][a] = sV[v][a];
+#pragma unroll
+        for (int c = 0; c < NE; ++c) En[c][a] = sV[NV + c][a];
+      }
+      const R* V0e[NV];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) V0e[v] = sV[NV + NE + 1 + v];
+      volume_element<DIM, P, R>(e, K, F, Vn, En, bed ? sV[NV + NE] : nullptr, V0e, out, geo, fid, wflux, ops, ph,
+                                ins, 1, c0, c1, sc);
+    }
+    __syncthreads();
+    buf ^= 1;
   }
 }
 
@@ -977,7 +1191,6 @@ void fill_ops(const RefOps& o, EstepOps<DIM, P, R>& eo, FaceOps<DIM, P, R>& fo, 
   for (int i = 0; i < S::NF * S::NFP; ++i) {
     eo.fmask[i] = (int8_t)o.fmask[i];
     fo.fmask[i] = (int8_t)o.fmask[i];
-    vo.fmask[i] = (int8_t)o.fmask[i];
   }
   for (int m = 0; m < S::NFQ; ++m) {
     fo.wf[m] = (R)o.wf[m];

@@ -63,8 +63,9 @@ def test_autotune_keeps_results():
     B1, _ = G.batch_from_cases(cases)
     B2, _ = G.batch_from_cases(cases)
     tiles = B2.autotune(3)
-    # per-face form of the face kernel is reported as a negative block size
-    assert all(abs(t) in (32, 64, 128, 256) and (t > 0 or k == 1) for g in tiles for k, t in enumerate(g))
+    # per-face form of the face kernel and staged form of the volume kernel
+    # are reported as negative block sizes
+    assert all(abs(t) in (32, 64, 128, 256) and (t > 0 or k in (1, 2)) for g in tiles for k, t in enumerate(g))
     B1.run(10)
     B2.run(10)
     for i in range(len(cases)):
@@ -92,3 +93,53 @@ def test_batch_nonfinite_names_instance():
     with pytest.raises(G.DGError) as ei:
         B.run(2)
     assert ei.value.status == G.DG_ERR_NONFINITE and "instance 1" in str(ei.value)
+
+
+def _run_with_volume_tiles(cases, precision, vol_tile, steps):
+    import paper_2301_11238_gb300 as G
+    B, _ = G.batch_from_cases(cases, precision=precision)
+    tiles = B.tiles()
+    B.set_tiles([[t[0], t[1], vol_tile] for t in tiles])
+    B.run(steps)
+    out = [B.get_state(i) for i in range(len(cases))]
+    B.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_staged_volume_bitwise_equal_to_direct(prec):
+    """The staged volume kernel (bulk copies into shared memory, negative
+    block size) does the same arithmetic as the direct one: bitwise equal
+    states after 12 steps, for 1D/2D groups of every order, with and
+    without a bed, through every RK stage (c0 = 0 and c0 != 0)."""
+    cases = _mixed_cases()
+    ref = _run_with_volume_tiles(cases, prec, 64, 12)
+    for T in (-32, -64, -128):
+        got = _run_with_volume_tiles(cases, prec, T, 12)
+        for i in range(len(cases)):
+            assert np.array_equal(got[i], ref[i]), (T, i, rel_l2(got[i], ref[i]))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_staged_volume_persistent_loop(prec):
+    """131,072 triangles: more tiles than resident blocks (4096 tiles of 32
+    against at most about 1,800 resident blocks), so every block walks
+    several tiles and the copy of its next tile overlaps the current one;
+    T = 96 leaves a ragged last tile."""
+    c = synth.radial_dam_2d(n=256, order=2, reg=1, sigma0=0.02)
+    ref = _run_with_volume_tiles([c], prec, 128, 3)[0]
+    for T in (-32, -96):
+        got = _run_with_volume_tiles([c], prec, T, 3)[0]
+        assert np.array_equal(got, ref), (T, rel_l2(got, ref))
+
+
+def test_staged_volume_rejects_oversized_tile():
+    import paper_2301_11238_gb300 as G
+    B, _ = G.batch_from_cases([synth.bump_dam_2d(n=4, order=3)])
+    t = B.tiles()[0]
+    with pytest.raises(G.DGError) as ei:
+        B.set_tiles([[t[0], t[1], -256]])  # 2 x 11 slots x 20 KB: beyond shared memory
+    assert ei.value.status == G.DG_ERR_ARG
+    B.set_tiles([[t[0], t[1], -32]])
+    B.run(2)
+    B.close()
