@@ -384,15 +384,56 @@ class Discretization:
 
     def ssp_rk3_step(self, Vh, dt=None):
         """One Shu-Osher SSP-RK3 step (explicit integrator for the
-        benchmark workloads; the paper itself integrates implicitly)."""
+        benchmark workloads; the paper itself integrates implicitly).  With
+        prm["positivity"] set, every stage result passes through
+        positivity_limit."""
+        lim = self.positivity_limit if self.prm.get("positivity", 0) else (lambda V: V)
         if dt is None:
             dt = self.stable_dt(Vh)
         k1, _ = self.rhs(Vh)
-        V1 = Vh + dt * k1
+        V1 = lim(Vh + dt * k1)
         k2, _ = self.rhs(V1)
-        V2 = 0.75 * Vh + 0.25 * (V1 + dt * k2)
+        V2 = lim(0.75 * Vh + 0.25 * (V1 + dt * k2))
         k3, _ = self.rhs(V2)
-        return Vh / 3.0 + 2.0 / 3.0 * (V2 + dt * k3), dt
+        return lim(Vh / 3.0 + 2.0 / 3.0 * (V2 + dt * k3)), dt
+
+    # ------------------------------------------------------------ wet/dry (extension)
+    def check_points(self, Vh_field):
+        """Values of one field at every point the depth limiter checks:
+        the equispaced nodes, the volume quadrature points and the face
+        quadrature points of every face; shape (K, n_points)."""
+        at_nodes = self.to_nodal(Vh_field)
+        at_vol = np.einsum("qa,ka->kq", self.Phi, Vh_field)
+        at_faces = np.einsum("fqa,ka->kfq", self.Phif, Vh_field).reshape(self.K, -1)
+        return np.concatenate([at_nodes, at_vol, at_faces], axis=1)
+
+    def positivity_limit(self, Vh):
+        """Depth limiter for wet/dry fronts.  Dry beds are left to future work
+        in the paper (Sec. 7); this is the scaling limiter of Zhang and Shu
+        (J. Comput. Phys. 229, 2010) applied to h, with the velocity set to
+        zero in dry elements.  Per element, with hbar the cell average of h
+        and m its minimum over check_points:
+          hbar <= 0:        h = 0;
+          m < 0 < hbar:     h <- hbar + theta (h - hbar), theta = hbar / (hbar - m)
+                            (the scaled polynomial has minimum 0 and the same mean);
+          otherwise:        h unchanged;
+        and u = 0 in elements with hbar < h_floor."""
+        V = Vh.copy()
+        h = Vh[0]
+        w = self.wJ
+        hbar = np.einsum("kq,kq->k", w, np.einsum("qa,ka->kq", self.Phi, h)) / w.sum(axis=1)
+        m = self.check_points(h).min(axis=1)
+        hn = self.to_nodal(h)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            theta = np.where(m < 0.0, hbar / (hbar - m), 1.0)
+        scaled = hbar[:, None] + theta[:, None] * (hn - hbar[:, None])
+        hn_new = np.where((hbar <= 0.0)[:, None], 0.0, np.where((m < 0.0)[:, None], scaled, hn))
+        changed = (hbar <= 0.0) | (m < 0.0)
+        V[0] = np.where(changed[:, None], self.to_modal(hn_new), h)
+        dry = hbar < self.prm["h_floor"]
+        for j in range(self.dim):
+            V[1 + j] = np.where(dry[:, None], 0.0, Vh[1 + j])
+        return V
 
     def total_mass(self, Vh):
         """Sum over elements of the integral of h (compensated summation)."""

@@ -1,4 +1,5 @@
-"""Exact solution of the 1D shallow-water Riemann problem (wet bed).
+"""Exact solutions of the 1D shallow-water dam break: the Riemann problem on
+a wet bed (Stoker) and the dam break onto a dry bed (Ritter).
 
 TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
 
@@ -67,4 +68,18 @@ def sample(x, t, x0, hl, ul, hr, ur, g):
                 else:
                     c = (-ur + 2.0 * cr + s) / 3.0
                     h[k], u[k] = c * c / g, (ur - 2.0 * cr + 2.0 * s) / 3.0
+    return h, u
+
+
+def ritter(x, t, x0, hl, g):
+    """(h, u) of the dam break onto a dry bed (Ritter): still water of depth hl
+    left of x0, dry bed right of it, t > 0.  With c = sqrt(g hl) and
+    xi = (x - x0) / t the rarefaction fan -c <= xi <= 2c carries
+    h = (2c - xi)^2 / (9 g), u = 2 (c + xi) / 3; left of it h = hl, u = 0,
+    right of the front xi = 2c the bed is dry (h = u = 0)."""
+    c = math.sqrt(g * hl)
+    xi = (np.asarray(x, dtype=float) - x0) / t
+    fan = (xi >= -c) & (xi <= 2.0 * c)
+    h = np.where(xi < -c, hl, np.where(fan, (2.0 * c - xi) ** 2 / (9.0 * g), 0.0))
+    u = np.where(fan, 2.0 * (c + xi) / 3.0, 0.0)
     return h, u
