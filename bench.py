@@ -55,6 +55,9 @@ def parse():
                     help="squares per side of the 2D mesh (radial 64, bump 512, slump 2048); "
                          "smaller values give profiling cases of the same kernels")
     ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--tiles", default=None,
+                    help="JSON list of [estep, face, volume] block sizes per group (encoded as in "
+                         "dg_batch_set_tiles) instead of the autotuner's choice; for profiling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
@@ -476,7 +479,11 @@ def main():
     with torch.cuda.stream(stream):
         if args.mode == "batch":
             batch, V0s = G.batch_from_cases(cases, precision=prec, stream=stream)
-            tiles = batch.autotune(5)
+            if args.tiles:
+                batch.set_tiles(json.loads(args.tiles))
+                tiles = batch.tiles()
+            else:
+                tiles = batch.autotune(5)
             units_per_inner = batch.info()["dofs"]
             launches_per_step = batch.launches_per_step() * args.inner
         else:

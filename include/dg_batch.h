@@ -56,15 +56,25 @@ dg_status dg_batch_run(dg_batch *b, int64_t n_steps, dg_swe_stats *stats);
 dg_status dg_batch_stats(dg_batch *b, dg_swe_stats *stats);
 
 /* Autotuner: for every group and each of the three stage kernels, times
- * thread-block sizes {32, 64, 128, 256} on the current state (n_iter
- * launches each, CUDA events) and keeps the fastest.  The face kernel also
- * tries its per-face form (one thread per face evaluating every edge point,
- * reported as a negative block size).  Synchronizes; the step
- * graph is recaptured on the next advance. */
+ * thread-block sizes T in {32, 64, 128, 256} on the current state (n_iter
+ * launches each, CUDA events) and keeps the fastest.  Kernel forms are
+ * encoded in the block-size entry:
+ *   face    T > 0: one thread per edge point;
+ *           -T: one thread per face evaluating every edge point;
+ *   volume  T > 0: one thread per element, nodal values read from global
+ *           memory; -T: staged: a persistent grid whose blocks bring the
+ *           next tile of T elements into shared memory with bulk
+ *           asynchronous copies while computing the current tile.
+ * Every form gives bitwise the same results.  Forms whose shared memory does
+ * not fit are skipped.  Synchronizes; the step graph is recaptured on the
+ * next advance. */
 dg_status dg_batch_autotune(dg_batch *b, int n_iter);
 /* Current block sizes: out[3*g + k], k = 0 E-step, 1 face, 2 volume; returns
  * the number of groups in *n_groups. */
 dg_status dg_batch_tiles(const dg_batch *b, int32_t *out, int cap, int32_t *n_groups);
+/* Sets the block sizes (encoded as for dg_batch_autotune), n = 3 x groups.
+ * DG_ERR_ARG for a size outside 32..256 or not a multiple of 32, or a
+ * shared-memory form that does not fit on the device for that group. */
 dg_status dg_batch_set_tiles(dg_batch *b, const int32_t *tiles, int n);
 
 /* Profiling aid: average device milliseconds of one launch of each kernel

@@ -103,6 +103,15 @@ typedef struct {
   int32_t precision;            /* DG_PREC_*                                             */
   int32_t n_bc;                 /* entries used in bc[] (>= 1)                           */
   dg_swe_bc bc[DG_SWE_MAX_BC];
+  int32_t positivity;           /* 1: depth limiter after every explicit stage (an
+                                   extension: the paper leaves wet/dry fronts to future
+                                   work, Sec. 7).  Per element, with hbar the cell average
+                                   of h and m the minimum of h over the nodes, volume and
+                                   face quadrature points: hbar <= 0 gives h = 0;
+                                   m < 0 < hbar scales h <- hbar + theta (h - hbar),
+                                   theta = hbar / (hbar - m) (Zhang-Shu scaling); the
+                                   velocity is set to 0 where hbar < h_floor.  Keeps
+                                   cell averages.  0: off (the paper's scheme)           */
 } dg_swe_params;
 
 typedef struct {

@@ -35,6 +35,7 @@ def make_params(prm, bcs=None, precision=PREC_FP64):
     for k in ("g", "rho", "alpha", "eta", "sigma0", "gamma", "beta", "pap_m", "h_floor", "cfl"):
         setattr(p, k, float(prm[k]))
     p.precision = int(precision)
+    p.positivity = int(prm.get("positivity", 0))
     bcs = bcs if bcs else [([0] * 7, [0.0] * 7)]
     if len(bcs) > _lib.MAX_BC:
         raise ValueError("too many boundary descriptors")

@@ -25,7 +25,8 @@ class Params(C.Structure):
     _fields_ = [("g", C.c_double), ("rho", C.c_double), ("alpha", C.c_double), ("eta", C.c_double),
                 ("sigma0", C.c_double), ("gamma", C.c_double), ("beta", C.c_double),
                 ("pap_m", C.c_double), ("h_floor", C.c_double), ("cfl", C.c_double),
-                ("precision", C.c_int32), ("n_bc", C.c_int32), ("bc", BC * MAX_BC)]
+                ("precision", C.c_int32), ("n_bc", C.c_int32), ("bc", BC * MAX_BC),
+                ("positivity", C.c_int32)]
 
 
 class Stats(C.Structure):

@@ -250,6 +250,7 @@ void push_phys(const dg_swe_params& p, int reg, std::vector<char>& out) {
   ph.pap_m = (R)p.pap_m;
   ph.h_floor = (R)p.h_floor;
   ph.reg = reg;
+  ph.pos = p.positivity ? 1 : 0;
   const char* c = reinterpret_cast<const char*>(&ph);
   out.insert(out.end(), c, c + sizeof(ph));
 }
@@ -789,7 +790,7 @@ dg_status dg_batch_set_tiles(dg_batch* b, const int32_t* tiles, int n) {
                    "block sizes must be 32..256, multiples of 32 (negative face entry: per-face form; negative "
                    "volume entry: staged form)");
     if (i % 3 == 2 && !b->groups[i / 3].drv->volume_ok(tiles[i]))
-      return bfail(b, DG_ERR_ARG, "staged volume block size " + std::to_string(-tiles[i]) +
+      return bfail(b, DG_ERR_ARG, "staged volume block size " + std::to_string(v) +
                                       " does not fit in shared memory for this group");
   }
   for (size_t g = 0; g < b->groups.size(); ++g)

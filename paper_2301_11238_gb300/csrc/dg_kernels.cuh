@@ -47,6 +47,7 @@ template <typename R>
 struct Phys {
   R gc, gs, rho_inv, eta, sigma0, gamma, beta, pap_m, h_floor;
   int reg;
+  int pos;  // depth limiter after every explicit stage (dg_swe_params.positivity)
 };
 
 // One boundary descriptor: per slot (V fields then E fields) a mode
@@ -86,6 +87,7 @@ struct VolOps {
   R wq[S::NQ];
   R Minv[S::NP * S::NP];
   R LfT[S::NFP * S::NFQ];  // Lf transposed: lift of face-point values to face nodes
+  R wavg[S::NP];           // cell average = sum_a wavg[a] h_a (integral of l_a / reference measure)
 };
 
 struct DevScalars {
@@ -461,12 +463,61 @@ __global__ void __launch_bounds__(256) face_kernel(int K, int F, const R* __rest
   const R wsj = fsj[fc];
   const size_t FQ = (size_t)F * NFQ;
   if (PERFACE) {
-#pragma unroll 1
+#pragma unroll
     for (int m = 0; m < NFQ; ++m)
       face_point<DIM, P, R>(m, Tm, Tp, interior, bct, -1 - e2, n, wsj, ops, ph, wflux, FQ,
                             (size_t)fc * NFQ + m);
   } else {
     face_point<DIM, P, R>(m0, Tm, Tp, interior, bct, -1 - e2, n, wsj, ops, ph, wflux, FQ, (size_t)tid);
+  }
+}
+
+// Depth limiter of one element's new stage values y (nodal), applied when
+// dg_swe_params.positivity is set (an extension for wet/dry fronts; Zhang-Shu
+// scaling of h): with hbar the cell average of h and m its minimum over the
+// nodes, the volume quadrature points and the face quadrature points,
+// hbar <= 0 gives h = 0, m < 0 < hbar gives h <- hbar + theta (h - hbar) with
+// theta = hbar / (hbar - m); the velocity is zeroed where hbar < h_floor.
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void positivity_limit(R (&y)[Sh<DIM, P>::NV][Sh<DIM, P>::NP], const VolOps<DIM, P, R>& ops,
+                                                 R h_floor) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NQ = S::NQ, NF = S::NF, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV;
+  R hbar = R(0), m = y[0][0];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    hbar += ops.wavg[a] * y[0][a];
+    m = fmin(m, y[0][a]);
+  }
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    R hq = R(0);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) hq += ops.Vq[q * NP + a] * y[0][a];
+    m = fmin(m, hq);
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int mq = 0; mq < NFQ; ++mq) {
+      R hf = R(0);
+#pragma unroll
+      for (int k = 0; k < NFP; ++k) hf += ops.LfT[k * NFQ + mq] * y[0][face_node(DIM, P, f, k)];
+      m = fmin(m, hf);
+    }
+  if (hbar <= R(0)) {
+#pragma unroll
+    for (int a = 0; a < NP; ++a) y[0][a] = R(0);
+  } else if (m < R(0)) {
+    const R theta = hbar / (hbar - m);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) y[0][a] = hbar + theta * (y[0][a] - hbar);
+  }
+  if (hbar < h_floor) {
+#pragma unroll
+    for (int v = 1; v < NV; ++v)
+#pragma unroll
+      for (int a = 0; a < NP; ++a) y[v][a] = R(0);
   }
 }
 
@@ -703,8 +754,13 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
         const R vi = Vn[v][a];
         R y = c1 * (vi + dt * dV[v][a]);
         if (c0 != R(0)) y += c0 * V0e[v][a];
-        out[v * KN + eo + a] = y;
+        dV[v][a] = y;
       }
+    if (ph.pos) positivity_limit<DIM, P, R>(dV, ops, ph.h_floor);
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int a = 0; a < NP; ++a) out[v * KN + eo + a] = dV[v][a];
   }
 }
 
@@ -1191,6 +1247,11 @@ void fill_ops(const RefOps& o, EstepOps<DIM, P, R>& eo, FaceOps<DIM, P, R>& fo, 
   for (int i = 0; i < S::NF * S::NFP; ++i) {
     eo.fmask[i] = (int8_t)o.fmask[i];
     fo.fmask[i] = (int8_t)o.fmask[i];
+  }
+  {
+    double area = 0.0;
+    for (int a = 0; a < NP; ++a) area += o.wint[a];
+    for (int a = 0; a < NP; ++a) vo.wavg[a] = (R)(o.wint[a] / area);
   }
   for (int m = 0; m < S::NFQ; ++m) {
     fo.wf[m] = (R)o.wf[m];

@@ -73,6 +73,7 @@ Phys<R> make_phys(const dg_swe_params& p, int reg) {
   ph.pap_m = (R)p.pap_m;
   ph.h_floor = (R)p.h_floor;
   ph.reg = reg;
+  ph.pos = p.positivity ? 1 : 0;
   return ph;
 }
 
