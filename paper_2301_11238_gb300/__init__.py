@@ -188,6 +188,52 @@ class Solver:
             pass
 
 
+class Newton:
+    """Backward Euler with a Jacobian-free Newton-Krylov solve on a Solver's
+    state (FP64; include/dg_newton.h).  ``run(n)`` advances n steps of size
+    dt and returns the solver statistics."""
+
+    def __init__(self, solver, dt, max_newton=10, rtol=1e-10, atol=1e-12, krylov_dim=30, krylov_rtol=1e-6,
+                 on_fail_continue=1):
+        torch = _torch()
+        self.L = solver.L
+        self.solver = solver  # the context must outlive this object
+        p = _lib.NewtonParams()
+        p.dt, p.max_newton, p.rtol, p.atol = float(dt), int(max_newton), float(rtol), float(atol)
+        p.krylov_dim, p.krylov_rtol, p.on_fail_continue = int(krylov_dim), float(krylov_rtol), int(on_fail_continue)
+        self._p = p
+        h = C.c_void_p()
+        st = self.L.dg_newton_init(solver.ctx, C.byref(p), C.byref(h))
+        if st != DG_OK:
+            raise DGError(st, "dg_newton_init")
+        self.h = h
+        nbytes = int(self.L.dg_newton_workspace_size(h))
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=solver.workspace.device)
+        self._check(self.L.dg_newton_set_workspace(h, C.c_void_p(self.workspace.data_ptr()), nbytes))
+
+    def _check(self, st):
+        if st != DG_OK:
+            raise DGError(st, self.L.dg_newton_last_error(self.h).decode())
+
+    def run(self, n_steps):
+        st = _lib.NewtonStats()
+        self._check(self.L.dg_newton_run(self.h, int(n_steps), C.byref(st)))
+        return dict(steps=st.steps, newton_its=st.newton_its, krylov_its=st.krylov_its,
+                    failed_steps=st.failed_steps, t=st.t, last_res=st.last_res, last_newton=st.last_newton,
+                    status=st.status)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.L.dg_newton_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def _stats_dict(st):
     return dict(steps=st.steps, t=st.t, dt_last=st.dt_last, dt_min=st.dt_min, dt_max=st.dt_max,
                 mass=st.mass, mass0=st.mass0, status=st.status)

@@ -71,7 +71,24 @@ _SIGS = {
     "dg_swe_destroy": (None, [C.c_void_p]),
 }
 
+class NewtonParams(C.Structure):
+    _fields_ = [("dt", C.c_double), ("max_newton", C.c_int32), ("rtol", C.c_double), ("atol", C.c_double),
+                ("krylov_dim", C.c_int32), ("krylov_rtol", C.c_double), ("on_fail_continue", C.c_int32)]
+
+
+class NewtonStats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("newton_its", C.c_int64), ("krylov_its", C.c_int64),
+                ("failed_steps", C.c_int64), ("t", C.c_double), ("last_res", C.c_double),
+                ("last_newton", C.c_int32), ("status", C.c_int32)]
+
+
 _OPTIONAL_SIGS = {
+    "dg_newton_init": (C.c_int, [C.c_void_p, C.POINTER(NewtonParams), C.POINTER(C.c_void_p)]),
+    "dg_newton_workspace_size": (C.c_size_t, [C.c_void_p]),
+    "dg_newton_set_workspace": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
+    "dg_newton_run": (C.c_int, [C.c_void_p, C.c_int64, C.POINTER(NewtonStats)]),
+    "dg_newton_last_error": (C.c_char_p, [C.c_void_p]),
+    "dg_newton_destroy": (None, [C.c_void_p]),
     "dg_implicit_init": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.POINTER(ImplicitParams),
                                    C.POINTER(C.c_void_p)]),
     "dg_implicit_workspace_size": (C.c_size_t, [C.c_void_p]),

@@ -10,8 +10,29 @@
 #include "../../include/dg_swe.h"
 #include "dg_host.h"
 
+struct dg_swe_ctx;
+
 namespace dgswe {
-struct Driver;
+// Kernel launches of one (dimension, order, precision) instantiation.
+struct Driver {
+  virtual ~Driver() = default;
+  virtual void estep(dg_swe_ctx* c, const void* V, void* E, cudaStream_t s) = 0;
+  virtual void face(dg_swe_ctx* c, const void* V, const void* E, cudaStream_t s) = 0;
+  virtual void volume(dg_swe_ctx* c, const void* Vin, const void* V0, void* out, int mode, double c0,
+                      double c1, cudaStream_t s) = 0;
+  virtual void dt_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
+  virtual void mass_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
+  // Face flux and residual-mode volume pass with caller-chosen scratch for
+  // the face fluxes and E (used by dg_swe_residual_static).
+  virtual void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) = 0;
+  virtual void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
+                             cudaStream_t s) = 0;
+  // Backward-Euler support (dg_newton.h): <l_a, U(V)> (mode 0) or
+  // out += (<l_a, U(V)> - Uold) * inv_dt (mode 1); z = scale M(V)^{-1} x.
+  virtual void be_time(dg_swe_ctx* c, const void* V, const void* Uold, void* out, double inv_dt, int mode,
+                       cudaStream_t s) = 0;
+  virtual void precond(dg_swe_ctx* c, const void* V, const void* x, void* z, double scale, cudaStream_t s) = 0;
+};
 struct DriverDeleter {
   void operator()(Driver* d) const;
 };

@@ -521,12 +521,104 @@ __device__ __forceinline__ void positivity_limit(R (&y)[Sh<DIM, P>::NV][Sh<DIM, 
   }
 }
 
+// Primitive-variable mass solve of one element (Appendix A, dU/dV):
+// dV = -M(V)^{-1} r, i.e. M dh/dt = -r_h and M_h du/dt = -r_u - M_u dh/dt,
+// with M_h = <psi, max(h, h_floor) psi> and M_u = <psi, u psi> at the volume
+// quadrature points; r in physical scaling, Jinv = 1 / J.
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void mass_solve_element(const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                                   const R (&r)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                                   const VolOps<DIM, P, R>& ops, R h_floor, R Jinv,
+                                                   R (&dV)[Sh<DIM, P>::NV][Sh<DIM, P>::NP]) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NQ = S::NQ;
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+    R acc = R(0);
+#pragma unroll
+    for (int b = 0; b < NP; ++b) acc += ops.Minv[a * NP + b] * r[0][b];
+    dV[0][a] = -acc * Jinv;
+  }
+  R Mh[NP][NP];
+  R rhs[DIM][NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = 0; b < NP; ++b) Mh[a][b] = R(0);
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) rhs[j][a] = -r[1 + j][a] * Jinv;
+  }
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    R hq = R(0), hdq = R(0), uq[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) uq[j] = R(0);
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const R l = ops.Vq[q * NP + a];
+      hq += l * Vn[0][a];
+      hdq += l * dV[0][a];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) uq[j] += l * Vn[1 + j][a];
+    }
+    const R wh = ops.wq[q] * fmax(hq, h_floor);
+    const R wd = ops.wq[q] * hdq;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const R la = ops.Vq[q * NP + a];
+      const R t = wh * la;
+#pragma unroll
+      for (int b = 0; b <= a; ++b) Mh[a][b] += t * ops.Vq[q * NP + b];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) rhs[j][a] -= wd * uq[j] * la;
+    }
+  }
+  // Cholesky of the reference-scaled M_h (lower triangle); the diagonal is
+  // kept as reciprocals so the factorization and both triangular solves
+  // multiply instead of divide (NP divisions per element instead of
+  // NP (NP + 3) / 2 + 2 DIM NP).
+  R dinv[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll
+    for (int b = 0; b < a; ++b) {
+      R s = Mh[a][b];
+#pragma unroll
+      for (int c = 0; c < b; ++c) s -= Mh[a][c] * Mh[b][c];
+      Mh[a][b] = s * dinv[b];
+    }
+    R d = Mh[a][a];
+#pragma unroll
+    for (int c = 0; c < a; ++c) d -= Mh[a][c] * Mh[a][c];
+    dinv[a] = dg_rsqrt<R>(d);
+  }
+#pragma unroll
+  for (int j = 0; j < DIM; ++j) {
+    R y[NP];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      R s = rhs[j][a];
+#pragma unroll
+      for (int c = 0; c < a; ++c) s -= Mh[a][c] * y[c];
+      y[a] = s * dinv[a];
+    }
+#pragma unroll
+    for (int a = NP - 1; a >= 0; --a) {
+      R s = y[a];
+#pragma unroll
+      for (int c = a + 1; c < NP; ++c) s -= Mh[c][a] * dV[1 + j][c];
+      dV[1 + j][a] = s * dinv[a];
+    }
+  }
+}
+
 // Everything the volume kernels do for one element e once its nodal values
 // are in registers: volume integrals, face lift, mass solve and output.
 // bed_e: the element's NP bed values (nullptr: flat bed).  V0e[v]: the
 // element's values of field v of the stage's first state (read in mode 1
 // when c0 != 0).  mode 0: write dV/dt to out; mode 1: out = c0 * V0 + c1 * (Vin +
-// dt * dV/dt).
+// dt * dV/dt); mode 2: write the spatial residual r_V of Eq. WeakForm51
+// (before the mass solve).
 template <int DIM, int P, typename R>
 __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
                                                const R (&En)[Sh<DIM, P>::NE][Sh<DIM, P>::NP],
@@ -657,87 +749,19 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
     }
   }
 
+  // mode 2: the spatial residual r_V itself (physical scaling), for the
+  // implicit integrators that assemble their own time term
+  if (mode == 2) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int a = 0; a < NP; ++a) out[v * KN + eo + a] = r[v][a];
+    return;
+  }
+
   // ---- mass solve: M dh/dt = -r_h ; M_h du/dt = -r_u - M_u dh/dt
-  const R Jinv = dg_div<R>(R(1), J);
   R dV[NV][NP];
-#pragma unroll
-  for (int a = 0; a < NP; ++a) {
-    R acc = R(0);
-#pragma unroll
-    for (int b = 0; b < NP; ++b) acc += ops.Minv[a * NP + b] * r[0][b];
-    dV[0][a] = -acc * Jinv;
-  }
-  R Mh[NP][NP];
-  R rhs[DIM][NP];
-#pragma unroll
-  for (int a = 0; a < NP; ++a) {
-#pragma unroll
-    for (int b = 0; b < NP; ++b) Mh[a][b] = R(0);
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) rhs[j][a] = -r[1 + j][a] * Jinv;
-  }
-#pragma unroll 1
-  for (int q = 0; q < NQ; ++q) {
-    R hq = R(0), hdq = R(0), uq[DIM];
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) uq[j] = R(0);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      const R l = ops.Vq[q * NP + a];
-      hq += l * Vn[0][a];
-      hdq += l * dV[0][a];
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) uq[j] += l * Vn[1 + j][a];
-    }
-    const R wh = ops.wq[q] * fmax(hq, ph.h_floor);
-    const R wd = ops.wq[q] * hdq;
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      const R la = ops.Vq[q * NP + a];
-      const R t = wh * la;
-#pragma unroll
-      for (int b = 0; b <= a; ++b) Mh[a][b] += t * ops.Vq[q * NP + b];
-#pragma unroll
-      for (int j = 0; j < DIM; ++j) rhs[j][a] -= wd * uq[j] * la;
-    }
-  }
-  // Cholesky of the reference-scaled M_h (lower triangle); the diagonal is
-  // kept as reciprocals so the factorization and both triangular solves
-  // multiply instead of divide (NP divisions per element instead of
-  // NP (NP + 3) / 2 + 2 DIM NP).
-  R dinv[NP];
-#pragma unroll
-  for (int a = 0; a < NP; ++a) {
-#pragma unroll
-    for (int b = 0; b < a; ++b) {
-      R s = Mh[a][b];
-#pragma unroll
-      for (int c = 0; c < b; ++c) s -= Mh[a][c] * Mh[b][c];
-      Mh[a][b] = s * dinv[b];
-    }
-    R d = Mh[a][a];
-#pragma unroll
-    for (int c = 0; c < a; ++c) d -= Mh[a][c] * Mh[a][c];
-    dinv[a] = dg_rsqrt<R>(d);
-  }
-#pragma unroll
-  for (int j = 0; j < DIM; ++j) {
-    R y[NP];
-#pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      R s = rhs[j][a];
-#pragma unroll
-      for (int c = 0; c < a; ++c) s -= Mh[a][c] * y[c];
-      y[a] = s * dinv[a];
-    }
-#pragma unroll
-    for (int a = NP - 1; a >= 0; --a) {
-      R s = y[a];
-#pragma unroll
-      for (int c = a + 1; c < NP; ++c) s -= Mh[c][a] * dV[1 + j][c];
-      dV[1 + j][a] = s * dinv[a];
-    }
-  }
+  mass_solve_element<DIM, P, R>(Vn, r, ops, ph.h_floor, dg_div<R>(R(1), J), dV);
 
   // ---- output
   if (mode == 0) {
@@ -796,6 +820,84 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
   for (int v = 0; v < NV; ++v) V0e[v] = V0 ? V0 + v * KN + eo : nullptr;
   volume_element<DIM, P, R>(e, K, F, Vn, En, bed ? bed + eo : nullptr, V0e, out, geo, fid, wflux, ops, ph, ins, mode,
                             c0, c1, sc);
+}
+
+// ------------------------------------------------------------------ backward Euler (Newton-Krylov)
+
+// <l_a, U_v(V)> per element in physical scaling, with U = (h, h u_1, ..,
+// h u_d) (Eq. Uterm) at the volume quadrature points.  mode 0: out = that;
+// mode 1: out += (that - Uold) * inv_dt, which adds the backward-Euler time
+// term of Eq. WeakForm7 to the spatial residual already in out.
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(256) be_time_kernel(int K, const R* __restrict__ V, const R* __restrict__ Uold,
+                                                      R* __restrict__ out, const R* __restrict__ geo,
+                                                      const VolOps<DIM, P, R> ops, R inv_dt, int mode) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NQ = S::NQ, NV = S::NV;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  const size_t KN = (size_t)K * NP, eo = (size_t)e * NP;
+  R Vn[NV][NP], acc[NV][NP];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      Vn[v][a] = V[v * KN + eo + a];
+      acc[v][a] = R(0);
+    }
+  const R J = geo[4 * K + e];
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    R Vq[NV];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      R t = R(0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) t += ops.Vq[q * NP + a] * Vn[v][a];
+      Vq[v] = t;
+    }
+    const R w = ops.wq[q] * J;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const R wl = w * ops.Vq[q * NP + a];
+      acc[0][a] += wl * Vq[0];
+#pragma unroll
+      for (int j = 1; j < NV; ++j) acc[j][a] += wl * (Vq[0] * Vq[j]);
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      const size_t i = v * KN + eo + a;
+      out[i] = mode == 0 ? acc[v][a] : out[i] + (acc[v][a] - Uold[i]) * inv_dt;
+    }
+}
+
+// z = scale * M(V)^{-1} x per element, M(V) the primitive-variable mass
+// matrix (Appendix A, dU/dV): the preconditioner of the Newton-Krylov solve.
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(256) mass_precond_kernel(int K, const R* __restrict__ V, const R* __restrict__ x,
+                                                           R* __restrict__ z, const R* __restrict__ geo,
+                                                           const VolOps<DIM, P, R> ops, R h_floor, R scale) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NV = S::NV;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  const size_t KN = (size_t)K * NP, eo = (size_t)e * NP;
+  R Vn[NV][NP], xr[NV][NP], dV[NV][NP];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      Vn[v][a] = V[v * KN + eo + a];
+      xr[v][a] = x[v * KN + eo + a];
+    }
+  mass_solve_element<DIM, P, R>(Vn, xr, ops, h_floor, dg_div<R>(R(1), geo[4 * K + e]), dV);
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) z[v * KN + eo + a] = -scale * dV[v][a];
 }
 
 // ------------------------------------------------------------------ staged volume kernel

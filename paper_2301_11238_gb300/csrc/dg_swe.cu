@@ -24,20 +24,6 @@ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 }  // namespace
 
 namespace dgswe {
-struct Driver {
-  virtual ~Driver() = default;
-  virtual void estep(dg_swe_ctx* c, const void* V, void* E, cudaStream_t s) = 0;
-  virtual void face(dg_swe_ctx* c, const void* V, const void* E, cudaStream_t s) = 0;
-  virtual void volume(dg_swe_ctx* c, const void* Vin, const void* V0, void* out, int mode, double c0,
-                      double c1, cudaStream_t s) = 0;
-  virtual void dt_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
-  virtual void mass_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
-  // Face flux and residual-mode volume pass with caller-chosen scratch for
-  // the face fluxes and E (used by dg_swe_residual_static).
-  virtual void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) = 0;
-  virtual void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
-                             cudaStream_t s) = 0;
-};
 void DriverDeleter::operator()(Driver* d) const { delete d; }
 }  // namespace dgswe
 
@@ -130,6 +116,17 @@ struct Impl final : Driver {
         K, F, (const R*)V, (const R*)E, c->at<int32_t>(c->off.fe1), c->at<int8_t>(c->off.ff1),
         c->at<int32_t>(c->off.fe2), c->at<int8_t>(c->off.ff2), c->at<R>(c->off.fnrm), c->at<R>(c->off.fsjf),
         (R*)wflux, fo, ph, nullptr, nullptr, c->at<BCEntry<R>>(c->off.bct));
+  }
+  void be_time(dg_swe_ctx* c, const void* V, const void* Uold, void* out, double inv_dt, int mode,
+               cudaStream_t s) override {
+    const int K = (int)c->mesh.K;
+    be_time_kernel<DIM, P, R><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+        K, (const R*)V, (const R*)Uold, (R*)out, c->at<R>(c->off.geo), vo, (R)inv_dt, mode);
+  }
+  void precond(dg_swe_ctx* c, const void* V, const void* x, void* z, double scale, cudaStream_t s) override {
+    const int K = (int)c->mesh.K;
+    mass_precond_kernel<DIM, P, R><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
+        K, (const R*)V, (const R*)x, (R*)z, c->at<R>(c->off.geo), vo, ph.h_floor, (R)scale);
   }
   void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
                      cudaStream_t s) override {
