@@ -247,6 +247,7 @@ void push_phys(const dg_swe_params& p, int reg, std::vector<char>& out) {
   ph.sigma0 = (R)p.sigma0;
   ph.gamma = (R)p.gamma;
   ph.beta = (R)p.beta;
+  ph.half_inv_beta = (R)(0.5 / p.beta);
   ph.pap_m = (R)p.pap_m;
   ph.h_floor = (R)p.h_floor;
   ph.reg = reg;

@@ -56,6 +56,7 @@ __device__ __forceinline__ void sigma1d(double e, const ImplArgs& a, double& sig
   ph.sigma0 = a.sigma0;
   ph.gamma = a.gamma;
   ph.beta = a.beta;
+  ph.half_inv_beta = 0.5 / a.beta;
   ph.pap_m = a.pap_m;
   ph.reg = a.reg;
   const double s = fabs(e);

@@ -46,6 +46,7 @@ struct Sh {
 template <typename R>
 struct Phys {
   R gc, gs, rho_inv, eta, sigma0, gamma, beta, pap_m, h_floor;
+  R half_inv_beta;  // 1 / (2 beta), the half-width of the regularizations 1 and 2 (host-computed)
   int reg;
   int pos;  // depth limiter after every explicit stage (dg_swe_params.positivity)
 };
@@ -98,15 +99,16 @@ struct DevScalars {
 };
 
 // ------------------------------------------------------------------ arithmetic helpers
-// FP64 keeps IEEE division and square root.  FP32 uses the fast hardware
-// forms (division, reciprocal square root and square root within 2 ulp),
-// well inside the FP32 path's stated tolerance.
+// FP64 keeps IEEE division and square root and uses the CUDA math library's
+// reciprocal square root (1 ulp).  FP32 uses the fast hardware forms
+// (division, reciprocal square root and square root within 2 ulp), well
+// inside the FP32 path's stated tolerance.
 template <typename R>
 __device__ __forceinline__ R dg_div(R a, R b) { return a / b; }
 template <>
 __device__ __forceinline__ float dg_div<float>(float a, float b) { return __fdividef(a, b); }
 template <typename R>
-__device__ __forceinline__ R dg_rsqrt(R x) { return R(1) / sqrt(x); }
+__device__ __forceinline__ R dg_rsqrt(R x) { return rsqrt(x); }
 template <>
 __device__ __forceinline__ float dg_rsqrt<float>(float x) { return rsqrtf(x); }
 template <typename R>
@@ -123,40 +125,46 @@ __device__ __forceinline__ float dg_sqrt<float>(float x) {
 // phi_k(s) / (2 s) for s >= 0 (limit phi_k'(0)/2 at s = 0): the Bingham
 // coefficient of sigma_B = (phi(s)/(2s)) (D + tr D I), s = ||D||_c / sqrt(2).
 template <typename R>
-__device__ __forceinline__ R bingham_coef(R s, const Phys<R>& ph) {
+__device__ __forceinline__ R bingham_coef(R s, R s_inv, const Phys<R>& ph) {
+  // s_inv = 1 / s (any value when s = 0: every s = 0 case takes a branch
+  // that does not use it)
   const R s0 = ph.sigma0, g = ph.gamma;
   if (ph.reg == 0 || s0 == R(0)) return R(0);
   switch (ph.reg) {
     case 1: {  // smooth max, Eq. sigmaTwoA/AA
-      R e = R(0.5) / ph.beta;
+      R e = ph.half_inv_beta;
       R x = g * s - s0;
       R mb = x >= e ? x : (x <= -e ? R(0) : R(0.5) * ph.beta * (x + e) * (x + e));
       return dg_div<R>(s0 * g, mb + s0);
     }
     case 2: {  // local quadratic, Eq. sigmaTwoB
-      R e = R(0.5) / ph.beta;
+      R e = ph.half_inv_beta;
       R x = g * s;
-      if (x >= s0 + e) return dg_div<R>(s0, s);
+      if (x >= s0 + e) return s0 * s_inv;
       if (x <= s0 - e) return g;
       R d = s0 - x + e;
-      return dg_div<R>(R(2) * s0 - ph.beta * d * d, R(2) * s);
+      return (R(2) * s0 - ph.beta * d * d) * (R(0.5) * s_inv);
     }
     case 3: {  // tanh, Eq. sigmaTwoC
       R x = g * s;
       if (x < R(1e-8)) return s0 * g * (R(1) - x * x / R(3));
-      return dg_div<R>(s0 * tanh(x), s);
+      return s0 * tanh(x) * s_inv;
     }
     case 4: {  // exponential (extension)
       R x = ph.pap_m * s;
       if (x < R(1e-12)) return s0 * ph.pap_m * (R(1) - R(0.5) * x);
-      return dg_div<R>(-s0 * expm1(-x), s);
+      return -s0 * expm1(-x) * s_inv;
     }
     case 5: {  // bi-viscosity (extension)
       R x = g * s;
-      return x < s0 ? g : dg_div<R>(s0, s);
+      return x < s0 ? g : s0 * s_inv;
     }
   }
   return R(0);
+}
+template <typename R>
+__device__ __forceinline__ R bingham_coef(R s, const Phys<R>& ph) {
+  return bingham_coef<R>(s, s > R(0) ? dg_div<R>(R(1), s) : R(0), ph);
 }
 
 // sigma from E (component 2i+j = du_j/dx_i); returns sig[i][j].
@@ -170,8 +178,11 @@ __device__ __forceinline__ void stress(const R* E, const Phys<R>& ph, R sig[DIM]
     R d11 = E[0], d22 = E[3], d12 = R(0.5) * (E[1] + E[2]);
     R tr = d11 + d22;
     R nc2 = d11 * d11 + R(2) * d12 * d12 + d22 * d22 + tr * tr;
-    R s = dg_sqrt<R>(R(0.5) * nc2);
-    R mu = R(2) * ph.eta + bingham_coef<R>(s, ph);
+    // s = sqrt(nc2 / 2) and 1 / s from one reciprocal square root
+    const R s2 = R(0.5) * nc2;
+    const R s_inv = s2 > R(0) ? dg_rsqrt<R>(s2) : R(0);
+    const R s = s2 * s_inv;
+    R mu = R(2) * ph.eta + bingham_coef<R>(s, s_inv, ph);
     sig[0][0] = mu * (d11 + tr);
     sig[1][1] = mu * (d22 + tr);
     sig[0][1] = mu * d12;

@@ -56,6 +56,7 @@ Phys<R> make_phys(const dg_swe_params& p, int reg) {
   ph.sigma0 = (R)p.sigma0;
   ph.gamma = (R)p.gamma;
   ph.beta = (R)p.beta;
+  ph.half_inv_beta = (R)(0.5 / p.beta);
   ph.pap_m = (R)p.pap_m;
   ph.h_floor = (R)p.h_floor;
   ph.reg = reg;
