@@ -464,7 +464,7 @@ def implicit_main(args):
             "roofline": {"bound": "latency", "kernel": "implicit_kernel<1,0> (one thread block)",
                          "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
                          "note": "one 100-element problem in one block: the Newton loop is a dependent "
-                                 "chain on one SM (see profiles/implicit_kernel_paper_dam_break_1d.md)",
+                                 "chain on one SM (the block-Thomas sweep is one warp)",
                          "ms_per_time_step": total_ms / steps_timed},
             "cpu_baseline": cpu, "e2e": None, "gpu_launches": args.steps,
             "clocks": clk.summary(), "accuracy": acc,

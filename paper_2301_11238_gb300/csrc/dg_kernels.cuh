@@ -83,6 +83,7 @@ struct VolOps {
   R Vq[S::NQ * S::NP];   // l_a(q)
   R Wr[S::NQ * S::NP];   // w_q dl_a/dr (q)
   R Ws[S::NQ * S::NP];   // w_q dl_a/ds (q)
+  R Wm[S::NQ * S::NP];   // w_q l_a(q)
   R Drq[S::NQ * S::NP];  // dl_a/dr (q) (bed gradient)
   R Dsq[S::NQ * S::NP];
   R wq[S::NQ];
@@ -420,11 +421,22 @@ __device__ __forceinline__ void face_point(int m, const R (&Tm)[Sh<DIM, P>::NV +
   for (int v = 0; v < NV; ++v) wflux[v * FQ + t] = w * (Fn[v] - R(0.5) * (Qm[v] + Qp[v]));
 }
 
+// Resident blocks of 256 threads the face kernel asks the compiler to fit
+// per SM: three (at most 85 registers a thread) for FP32 at p <= 2, where
+// the latency-bound gathers gain from the extra warps (per-face form on 2M
+// triangles: 0.235 -> 0.203 ms, with a 16-byte spill); otherwise the
+// compiler's choice (FP64 and p = 3 would spill heavily).
+template <int DIM, int P, typename R>
+constexpr int face_min_blocks() {
+  return (sizeof(R) == 4 && P <= 2) ? 3 : 1;
+}
+
 // PERFACE = false: one thread per face point (re-reads the face-node traces
 // for every point); PERFACE = true: one thread per face, traces read once
 // and all edge points evaluated in turn.  Same arithmetic per point.
 template <int DIM, int P, typename R, bool BATCH, bool PERFACE>
-__global__ void __launch_bounds__(256) face_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E,
+__global__ void __launch_bounds__(256, face_min_blocks<DIM, P, R>())
+    face_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E,
                                                    const int32_t* __restrict__ fe1, const int8_t* __restrict__ ff1,
                                                    const int32_t* __restrict__ fe2, const int8_t* __restrict__ ff2,
                                                    const R* __restrict__ fnrm, const R* __restrict__ fsj,
@@ -657,6 +669,12 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 #pragma unroll
     for (int a = 0; a < NP; ++a) r[v][a] = R(0);
 
+  // the element's bed values, read once
+  const bool has_bed = bed_e != nullptr;
+  R Hn[NP];
+#pragma unroll
+  for (int a = 0; a < NP; ++a) Hn[a] = has_bed ? bed_e[a] : R(0);
+
   // ---- volume integrals: -<grad N, F - Q> - <N, S>  (Eq. WeakForm51)
 #pragma unroll 1
   for (int q = 0; q < NQ; ++q) {
@@ -673,13 +691,13 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
       for (int v = 0; v < NV; ++v) Vq[v] += l * Vn[v][a];
 #pragma unroll
       for (int c = 0; c < NE; ++c) Eq[c] += l * En[c][a];
-      if (bed_e) {
-        const R H = bed_e[a];
-        Hr += ops.Drq[q * NP + a] * H;
-        if constexpr (DIM == 2) Hs += ops.Dsq[q * NP + a] * H;
+      if (has_bed) {
+        Hr += ops.Drq[q * NP + a] * Hn[a];
+        if constexpr (DIM == 2) Hs += ops.Dsq[q * NP + a] * Hn[a];
       }
     }
     const R h = Vq[0];
+    const R hr = h * ph.rho_inv;
     R sig[DIM][DIM];
     stress<DIM, R>(Eq, ph, sig);
     R fx[DIM][NV];  // (Q - F) in direction i
@@ -687,8 +705,7 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
     for (int i = 0; i < DIM; ++i) {
       fx[i][0] = -h * Vq[1 + i];
 #pragma unroll
-      for (int j = 0; j < DIM; ++j)
-        fx[i][1 + j] = -h * Vq[1 + i] * Vq[1 + j] + h * sig[j][i] * ph.rho_inv;
+      for (int j = 0; j < DIM; ++j) fx[i][1 + j] = -h * Vq[1 + i] * Vq[1 + j] + hr * sig[j][i];
       fx[i][1 + i] -= R(0.5) * ph.gc * h * h;
     }
     R Sv[NV];
@@ -718,10 +735,11 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
     for (int a = 0; a < NP; ++a) {
       const R wr = ops.Wr[q * NP + a];
       const R ws = ops.Ws[q * NP + a];
-      const R wm = ops.wq[q] * ops.Vq[q * NP + a];
+      const R wm = ops.Wm[q * NP + a];
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        R acc = wr * fr[v] - wm * Sv[v];
+        R acc = wr * fr[v];
+        if (v > 0) acc -= wm * Sv[v];  // the depth equation has no source
         if constexpr (DIM == 2) acc += ws * fs[v];
         r[v][a] += acc;
       }
@@ -1381,6 +1399,7 @@ void fill_ops(const RefOps& o, EstepOps<DIM, P, R>& eo, FaceOps<DIM, P, R>& fo, 
       vo.Dsq[q * NP + a] = (R)o.Dsq[q * NP + a];
       vo.Wr[q * NP + a] = (R)(o.wq[q] * o.Drq[q * NP + a]);
       vo.Ws[q * NP + a] = (R)(o.wq[q] * o.Dsq[q * NP + a]);
+      vo.Wm[q * NP + a] = (R)(o.wq[q] * o.Vq[q * NP + a]);
     }
   }
 }
