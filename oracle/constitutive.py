@@ -21,6 +21,12 @@ s = ||D||_c / sqrt(2) (||.||_c of Eq. bingham; s = |E| in 1D) the Bingham part
 is sigma_B = phi(s) / (2 s) (D + tr D I).  This equals Eq. bingham2 when phi is
 the unregularized 2 sigma0, and reduces to the paper's 1D functions in 1D.
 sigma0 = 0 gives sigma_B = 0 for every regularization.
+
+Herschel-Bulkley extension (the paper's introduction cites the law; its
+scheme is Bingham): with prm["flow_index"] = n in (0, 1) the Newtonian
+viscosity eta becomes the power law eta max(s, prm["rate_floor"])^(n - 1)
+(eta read as the consistency, s as above); n = 1 (or absent) is the paper's
+Newtonian part.
 """
 import numpy as np
 
@@ -95,6 +101,29 @@ def phi_over_2s(s, prm):
     return np.where(s > 0.0, q, lim)
 
 
+def flow_index(prm):
+    n = float(prm.get("flow_index", 1.0))
+    return 1.0 if n == 0.0 else n
+
+
+def viscosity(s, prm):
+    """Viscosity of the Newtonian part at strain-rate measure s: eta, or
+    eta max(s, rate_floor)^(n - 1) for the Herschel-Bulkley extension."""
+    s = np.asarray(s, dtype=float)
+    n = flow_index(prm)
+    if n == 1.0:
+        return np.full_like(s, prm["eta"])
+    return prm["eta"] * np.maximum(s, prm["rate_floor"]) ** (n - 1.0)
+
+
+def max_viscosity(prm):
+    """Largest d sigma_N / dE over E, divided by 4 (1D): eta, or
+    eta rate_floor^(n - 1) for 0 < n < 1, where the slope below the floor,
+    4 eta rate_floor^(n - 1), exceeds the slope 4 eta n E^(n - 1) above it."""
+    n = flow_index(prm)
+    return prm["eta"] if n == 1.0 else prm["eta"] * prm["rate_floor"] ** (n - 1.0)
+
+
 def max_slope(prm):
     """Largest d sigma_B / dE over E (attained at E = 0 for every
     regularization here)."""
@@ -107,11 +136,10 @@ def stress(E, dim, prm):
     E has shape (dim*dim, ...) with component 2*i + j (1D: 0) equal to
     E_ij = d u_j / d x_i (Eq. gradientVel).  Returns sigma as (dim, dim, ...)
     (symmetric)."""
-    eta = prm["eta"]
     if dim == 1:
         e = E[0]
         s = np.abs(e)
-        mu = 2.0 * eta + phi_over_2s(s, prm)
+        mu = 2.0 * viscosity(s, prm) + phi_over_2s(s, prm)
         return (mu * 2.0 * e)[None, None]
     d11 = E[0]
     d22 = E[3]
@@ -121,7 +149,7 @@ def stress(E, dim, prm):
     t12 = d12
     nc2 = d11 ** 2 + 2.0 * d12 ** 2 + d22 ** 2 + (d11 + d22) ** 2
     s = np.sqrt(0.5 * nc2)
-    mu = 2.0 * eta + phi_over_2s(s, prm)
+    mu = 2.0 * viscosity(s, prm) + phi_over_2s(s, prm)
     sig = np.empty((2, 2) + np.shape(d11))
     sig[0, 0] = mu * t11
     sig[1, 1] = mu * t22
@@ -131,5 +159,7 @@ def stress(E, dim, prm):
 
 
 def dsigma_dE_1d(e, prm):
-    """d sigma / dE in 1D: 4 eta + phi'(|E|) (Appendix A)."""
+    """d sigma / dE in 1D: 4 eta + phi'(|E|) (Appendix A; Newtonian viscous
+    part only)."""
+    assert flow_index(prm) == 1.0, "the Appendix A tangent covers the Newtonian viscous part"
     return 4.0 * prm["eta"] + dphi(np.abs(e), prm)

@@ -365,14 +365,16 @@ class Discretization:
 
     # ------------------------------------------------------------ time stepping
     def max_diffusivity(self):
-        return (4.0 * self.prm["eta"] + C.max_slope(self.prm)) / self.prm["rho"]
+        return (4.0 * C.max_viscosity(self.prm) + C.max_slope(self.prm)) / self.prm["rho"]
 
     def stable_dt(self, Vh):
         """Explicit step bound (reading of the paper's silence on explicit
         stepping): per element
             dt_e = cfl * dx_e / ((2p+1) lam_e + (2p+1)^2 * 2 nu / dx_e)
         with lam_e the largest |u| + sqrt(g_c max(h, h_floor)) over the
-        element's nodes and nu = (4 eta + max d sigma_B/dE) / rho; dt is the
+        element's nodes and nu = (4 eta_max + max d sigma_B/dE) / rho (eta_max
+        the largest viscous slope / 4: eta, or the Herschel-Bulkley
+        eta rate_floor^(n-1)); dt is the
         minimum over elements."""
         Vn = self.to_nodal(Vh)
         sp = np.sqrt(sum(Vn[1 + j] ** 2 for j in range(self.dim)))
