@@ -66,8 +66,9 @@ typedef struct {
   int32_t status;            /* latched dg_status                                 */
 } dg_implicit_stats;
 
-/* 1D mesh only (DG_ERR_UNSUPPORTED otherwise, or if the mesh is not ordered
- * left to right).  Copies the host inputs. */
+/* 1D mesh only (DG_ERR_UNSUPPORTED otherwise, if the mesh is not ordered
+ * left to right, or for a Herschel-Bulkley viscous part, flow_index != 1,
+ * which the Appendix A tangent does not cover).  Copies the host inputs. */
 dg_status dg_implicit_init(const dg_swe_mesh *mesh, int order, int regularization,
                            const dg_swe_params *params, const dg_implicit_params *ip,
                            dg_implicit **out);

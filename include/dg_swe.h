@@ -112,6 +112,15 @@ typedef struct {
                                    theta = hbar / (hbar - m) (Zhang-Shu scaling); the
                                    velocity is set to 0 where hbar < h_floor.  Keeps
                                    cell averages.  0: off (the paper's scheme)           */
+  double flow_index;            /* n of a Herschel-Bulkley viscous part (an extension; the
+                                   paper's introduction cites the law, its scheme is
+                                   Bingham): the Newtonian 2 eta (D + tr D I) becomes
+                                   2 eta max(s, rate_floor)^(n-1) (D + tr D I), eta the
+                                   consistency, s = ||D||_c / sqrt(2) (|E| in 1D).
+                                   0 or 1: Newtonian (the paper); 0 < n < 1: shear
+                                   thinning; other values DG_ERR_ARG                     */
+  double rate_floor;            /* s below which the power-law viscosity is frozen
+                                   (> 0 when 0 < flow_index < 1)                         */
 } dg_swe_params;
 
 typedef struct {

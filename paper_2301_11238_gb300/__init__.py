@@ -36,6 +36,8 @@ def make_params(prm, bcs=None, precision=PREC_FP64):
         setattr(p, k, float(prm[k]))
     p.precision = int(precision)
     p.positivity = int(prm.get("positivity", 0))
+    p.flow_index = float(prm.get("flow_index", 1.0))
+    p.rate_floor = float(prm.get("rate_floor", 0.0))
     bcs = bcs if bcs else [([0] * 7, [0.0] * 7)]
     if len(bcs) > _lib.MAX_BC:
         raise ValueError("too many boundary descriptors")

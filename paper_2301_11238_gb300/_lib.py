@@ -26,7 +26,7 @@ class Params(C.Structure):
                 ("sigma0", C.c_double), ("gamma", C.c_double), ("beta", C.c_double),
                 ("pap_m", C.c_double), ("h_floor", C.c_double), ("cfl", C.c_double),
                 ("precision", C.c_int32), ("n_bc", C.c_int32), ("bc", BC * MAX_BC),
-                ("positivity", C.c_int32)]
+                ("positivity", C.c_int32), ("flow_index", C.c_double), ("rate_floor", C.c_double)]
 
 
 class Stats(C.Structure):

@@ -252,6 +252,9 @@ void push_phys(const dg_swe_params& p, int reg, std::vector<char>& out) {
   ph.h_floor = (R)p.h_floor;
   ph.reg = reg;
   ph.pos = p.positivity ? 1 : 0;
+  ph.hb = (p.flow_index != 0.0 && p.flow_index != 1.0) ? 1 : 0;
+  ph.hb_n = (R)(ph.hb ? p.flow_index : 1.0);
+  ph.hb_floor = (R)p.rate_floor;
   const char* c = reinterpret_cast<const char*>(&ph);
   out.insert(out.end(), c, c + sizeof(ph));
 }
@@ -418,7 +421,8 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
     iparm.push_back(pp.g * std::cos(pp.alpha));
     iparm.push_back(pp.h_floor);
     iparm.push_back(pp.cfl);
-    iparm.push_back((4.0 * pp.eta + max_bingham_slope(regs[i], pp.sigma0, pp.gamma, pp.pap_m)) / pp.rho);
+    iparm.push_back((4.0 * max_viscous_eta(pp) + max_bingham_slope(regs[i], pp.sigma0, pp.gamma, pp.pap_m)) /
+                    pp.rho);
     dg_swe_destroy(c);
   }
   // interleave per-member SoA blocks into group SoA arrays

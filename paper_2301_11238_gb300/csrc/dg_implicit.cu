@@ -992,6 +992,12 @@ dg_status dg_implicit_init(const dg_swe_mesh* mesh, int order, int regularizatio
     *out = s.release();
     return ifail(*out, DG_ERR_ARG, "continuation needs gamma0 > 0");
   }
+  if (params->flow_index != 0.0 && params->flow_index != 1.0) {
+    *out = s.release();
+    return ifail(*out, DG_ERR_UNSUPPORTED,
+                 "the Appendix A tangent covers the Newtonian viscous part only (flow_index 1); "
+                 "use dg_newton.h for the Herschel-Bulkley law");
+  }
   if (ip->linear_solver == 1 && 3 * (2 * (order + 1) + m3 + 1) > 32) {
     *out = s.release();
     return ifail(*out, DG_ERR_UNSUPPORTED, "the FP32 factorization handles blocks of at most 10 unknowns (2(p+1) + m3 + 1 <= 10)");

@@ -47,6 +47,8 @@ template <typename R>
 struct Phys {
   R gc, gs, rho_inv, eta, sigma0, gamma, beta, pap_m, h_floor;
   R half_inv_beta;  // 1 / (2 beta), the half-width of the regularizations 1 and 2 (host-computed)
+  R hb_n, hb_floor;  // Herschel-Bulkley flow index and rate floor (dg_swe_params)
+  int hb;            // 1: power-law viscous part (flow index != 1)
   int reg;
   int pos;  // depth limiter after every explicit stage (dg_swe_params.positivity)
 };
@@ -168,12 +170,19 @@ __device__ __forceinline__ R bingham_coef(R s, const Phys<R>& ph) {
   return bingham_coef<R>(s, s > R(0) ? dg_div<R>(R(1), s) : R(0), ph);
 }
 
+// Viscosity of the Newtonian part: eta, or the Herschel-Bulkley power law
+// eta max(s, rate_floor)^(n-1) (dg_swe_params.flow_index, an extension).
+template <typename R>
+__device__ __forceinline__ R viscous_eta(R s, const Phys<R>& ph) {
+  return ph.hb ? ph.eta * pow(fmax(s, ph.hb_floor), ph.hb_n - R(1)) : ph.eta;
+}
+
 // sigma from E (component 2i+j = du_j/dx_i); returns sig[i][j].
 template <int DIM, typename R>
 __device__ __forceinline__ void stress(const R* E, const Phys<R>& ph, R sig[DIM][DIM]) {
   if constexpr (DIM == 1) {
     R e = E[0];
-    R mu = R(2) * ph.eta + bingham_coef<R>(fabs(e), ph);
+    R mu = R(2) * viscous_eta<R>(fabs(e), ph) + bingham_coef<R>(fabs(e), ph);
     sig[0][0] = mu * R(2) * e;
   } else {
     R d11 = E[0], d22 = E[3], d12 = R(0.5) * (E[1] + E[2]);
@@ -183,7 +192,7 @@ __device__ __forceinline__ void stress(const R* E, const Phys<R>& ph, R sig[DIM]
     const R s2 = R(0.5) * nc2;
     const R s_inv = s2 > R(0) ? dg_rsqrt<R>(s2) : R(0);
     const R s = s2 * s_inv;
-    R mu = R(2) * ph.eta + bingham_coef<R>(s, s_inv, ph);
+    R mu = R(2) * viscous_eta<R>(s, ph) + bingham_coef<R>(s, s_inv, ph);
     sig[0][0] = mu * (d11 + tr);
     sig[1][1] = mu * (d22 + tr);
     sig[0][1] = mu * d12;
@@ -1405,6 +1414,15 @@ void fill_ops(const RefOps& o, EstepOps<DIM, P, R>& eo, FaceOps<DIM, P, R>& fo, 
 }
 
 // Maximum d sigma_B / dE over E (attained at E = 0) for the step bound.
+// Largest d sigma_N / dE of the viscous part over E, divided by 4: eta, or
+// eta rate_floor^(n-1) for the Herschel-Bulkley power law with 0 < n < 1
+// (its slope 4 eta n |E|^(n-1) above the floor is smaller).
+inline double max_viscous_eta(const dg_swe_params& p) {
+  const double n = p.flow_index;
+  if (n == 0.0 || n == 1.0) return p.eta;
+  return p.eta * std::pow(p.rate_floor, n - 1.0);
+}
+
 inline double max_bingham_slope(int reg, double sigma0, double gamma, double pap_m) {
   if (!(sigma0 > 0.0)) return 0.0;
   switch (reg) {

@@ -61,6 +61,9 @@ Phys<R> make_phys(const dg_swe_params& p, int reg) {
   ph.h_floor = (R)p.h_floor;
   ph.reg = reg;
   ph.pos = p.positivity ? 1 : 0;
+  ph.hb = (p.flow_index != 0.0 && p.flow_index != 1.0) ? 1 : 0;
+  ph.hb_n = (R)(ph.hb ? p.flow_index : 1.0);
+  ph.hb_floor = (R)p.rate_floor;
   return ph;
 }
 
@@ -141,7 +144,7 @@ struct Impl final : Driver {
     const int K = (int)c->mesh.K;
     const auto& p = c->prm;
     const double slope = max_bingham_slope(c->reg, p.sigma0, p.gamma, p.pap_m);
-    const double nu = (4.0 * p.eta + slope) / p.rho;
+    const double nu = (4.0 * max_viscous_eta(p) + slope) / p.rho;
     dt_partial_kernel<DIM, P, R><<<c->nblk_dt, kRedBlock, 0, s>>>(
         K, (const R*)V, c->at<R>(c->off.geo), p.g * std::cos(p.alpha), p.h_floor, p.cfl, nu,
         c->at<double>(c->off.partial));
@@ -271,6 +274,11 @@ dg_status dg_swe_init(const dg_swe_mesh* mesh, int order, int regularization, co
   if (regularization == 2 && p.sigma0 > 0 && p.sigma0 < 0.5 / p.beta) {
     *out = c.release();
     return fail(*out, DG_ERR_ARG, "local quadratic regularization needs sigma0 >= 1/(2 beta)");
+  }
+  if (!(p.flow_index == 0.0 || p.flow_index == 1.0 ||
+        (p.flow_index > 0.0 && p.flow_index < 1.0 && p.rate_floor > 0.0))) {
+    *out = c.release();
+    return fail(*out, DG_ERR_ARG, "flow_index must be 0 or 1 (Newtonian) or in (0, 1) with rate_floor > 0");
   }
   if (regularization == 4 && p.sigma0 > 0 && !(p.pap_m > 0)) {
     *out = c.release();
