@@ -102,7 +102,8 @@ struct GDrv final : GroupDrv {
   FaceOps<DIM, P, R> fo{};
   VolOps<DIM, P, R> vo{};
   int n_sm = 0;
-  size_t smem_optin = 0;
+  size_t smem_optin = 0;     // shared memory a block may use (static + dynamic)
+  size_t staged_static = 0;  // the staged kernel's static shared memory
   std::map<int, int> staged_grid;  // staged volume block size -> persistent grid size (0: not launchable)
   explicit GDrv(const RefOps& o) {
     fill_ops<DIM, P, R>(o, eo, fo, vo);
@@ -112,9 +113,12 @@ struct GDrv final : GroupDrv {
       if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) == cudaSuccess)
         smem_optin = (size_t)v;
     }
-    if (smem_optin)
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, volume_staged_kernel<DIM, P, R>) == cudaSuccess)
+      staged_static = fa.sharedSizeBytes;
+    if (smem_optin > staged_static)
       cudaFuncSetAttribute(volume_staged_kernel<DIM, P, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)smem_optin);
+                           (int)(smem_optin - staged_static));
     cudaGetLastError();
   }
   // persistent grid of the staged volume kernel: resident blocks per SM x SMs
@@ -123,7 +127,7 @@ struct GDrv final : GroupDrv {
     if (it != staged_grid.end()) return it->second;
     int nb = 0;
     const size_t smem = staged_smem_bytes<DIM, P, R>(T);
-    if (n_sm > 0 && smem <= smem_optin &&
+    if (n_sm > 0 && smem + staged_static <= smem_optin &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, volume_staged_kernel<DIM, P, R>, T, smem) != cudaSuccess)
       nb = 0;
     cudaGetLastError();
