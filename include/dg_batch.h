@@ -50,9 +50,13 @@ dg_status dg_batch_get_state(dg_batch *b, int i, double *V, int on_device);
 /* Enqueue n_steps SSP-RK3 steps of every instance (each with its own
  * CFL-limited step), replayed from a CUDA graph captured on first use. */
 dg_status dg_batch_advance(dg_batch *b, int64_t n_steps);
-/* dg_batch_advance + per-instance mass reduction + synchronize; stats[n] may be NULL. */
+/* dg_batch_advance + per-instance mass reduction + synchronize; stats[n] may be NULL.
+ * A latched device status of an instance is returned with its index in the
+ * message: DG_ERR_NONFINITE (non-finite state) or DG_ERR_TIMEOUT (a bounded
+ * wait of the staged volume kernel for its bulk copies ran out). */
 dg_status dg_batch_run(dg_batch *b, int64_t n_steps, dg_swe_stats *stats);
-/* Mass reduction + synchronize; fills stats[n]. */
+/* Mass reduction + synchronize; fills stats[n]; reports latched statuses as
+ * dg_batch_run does. */
 dg_status dg_batch_stats(dg_batch *b, dg_swe_stats *stats);
 
 /* Autotuner: for every group and each of the three stage kernels, times
