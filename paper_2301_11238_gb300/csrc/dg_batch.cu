@@ -95,6 +95,53 @@ dg_status bcuda(dg_batch* b, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return bcuda(b, e_, #call);   \
   } while (0)
 
+// Integral of h per instance, in two fixed-order passes so that repeated
+// calls give identical sums: one block per 256-element range of one
+// instance (the step-size blocks) writes its FP64 partial, then one warp per
+// instance adds its blocks' partials.  (A single block per instance left a
+// whole SM reducing an 8.4M-element instance: 35 ms per set_state.)
+template <int NP, typename R>
+__global__ void __launch_bounds__(256) mass_block_kernel(int K, int b0, const int64_t* __restrict__ blk_e,
+                                                         const R* __restrict__ V, const R* __restrict__ geo,
+                                                         const double* __restrict__ wint,
+                                                         double* __restrict__ partial) {
+  __shared__ double red[8];
+  const int b = b0 + blockIdx.x;
+  const int64_t e = blk_e[b] + threadIdx.x;
+  double v = 0.0;
+  if (e < blk_e[b + 1]) {
+    double sum = 0.0;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) sum += wint[a] * (double)V[(size_t)e * NP + a];
+    v = (double)geo[4 * (size_t)K + e] * sum;
+  }
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
+    partial[b] = t;
+  }
+}
+
+static __global__ void mass_members_kernel(int first, int count, const int32_t* __restrict__ mblk,
+                                           const int32_t* __restrict__ gid, const double* __restrict__ partial,
+                                           int set_ref, DevScalars* __restrict__ sc) {
+  const int i = first + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (i >= first + count) return;
+  double m = 0.0;
+  for (int b = mblk[i] + lane; b < mblk[i + 1]; b += 32) m += partial[b];
+  m = warp_sum(m);
+  if (lane == 0) {
+    DevScalars& d = sc[gid[i]];
+    d.mass = m;
+    if (set_ref) d.mass0 = m;
+  }
+}
+
 template <int DIM, int P, typename R>
 struct GDrv final : GroupDrv {
   using S = Sh<DIM, P>;
@@ -196,9 +243,16 @@ struct GDrv final : GroupDrv {
                                                    b->at<double>(g.off.partial), b->at<DevScalars>(b->off_sc));
   }
   void mass(dg_batch* b, Group& g, int first, int count, int set_ref, cudaStream_t s) override {
-    mass_instance_kernel<S::NP, R><<<(unsigned)count, 256, 0, s>>>(
-        (int)g.K, b->at<int64_t>(g.off.ebeg) + first, b->at<int32_t>(g.off.gid) + first, b->at<R>(g.off.V[0]),
-        b->at<R>(g.off.geo), b->at<double>(g.off.wint), set_ref, b->at<DevScalars>(b->off_sc));
+    if (count <= 0) return;
+    const int b0 = g.mblk[first], nb = g.mblk[first + count] - b0;
+    if (nb > 0)
+      mass_block_kernel<S::NP, R><<<(unsigned)nb, 256, 0, s>>>((int)g.K, b0, b->at<int64_t>(g.off.blk_e),
+                                                              b->at<R>(g.off.V[0]), b->at<R>(g.off.geo),
+                                                              b->at<double>(g.off.wint), b->at<double>(g.off.partial));
+    mass_members_kernel<<<(unsigned)((count + 7) / 8), 256, 0, s>>>(first, count, b->at<int32_t>(g.off.mblk),
+                                                                   b->at<int32_t>(g.off.gid),
+                                                                   b->at<double>(g.off.partial), set_ref,
+                                                                   b->at<DevScalars>(b->off_sc));
   }
 };
 

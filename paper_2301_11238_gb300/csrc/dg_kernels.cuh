@@ -1421,37 +1421,6 @@ static __global__ void dt_members_kernel(int n_members, const int32_t* __restric
   }
 }
 
-// One block per instance: FP64 integral of h over the instance (fixed
-// reduction order, so repeated calls give identical sums).
-template <int NP, typename R>
-__global__ void __launch_bounds__(256) mass_instance_kernel(int K, const int64_t* __restrict__ ebeg,
-                                                            const int32_t* __restrict__ gid,
-                                                            const R* __restrict__ V, const R* __restrict__ geo,
-                                                            const double* __restrict__ wint, int set_ref,
-                                                            DevScalars* __restrict__ sc) {
-  __shared__ double red[8];
-  const int i = blockIdx.x;
-  const int64_t b = ebeg[i], en = ebeg[i + 1];
-  double acc = 0.0;
-  for (int64_t e = b + threadIdx.x; e < en; e += blockDim.x) {
-    double s = 0.0;
-#pragma unroll
-    for (int a = 0; a < NP; ++a) s += wint[a] * (double)V[(size_t)e * NP + a];
-    acc += (double)geo[4 * K + e] * s;
-  }
-  double v = warp_sum(acc);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += red[k];
-    DevScalars& s = sc[gid[i]];
-    s.mass = t;
-    if (set_ref) s.mass0 = t;
-  }
-}
-
 static __global__ void reset_scalars_array_kernel(int n, DevScalars* sc) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
