@@ -1,18 +1,24 @@
 #!/usr/bin/env python
 """Throughput benchmark of the DG shallow-water / regularized-Bingham hot path.
 
-Workload (default): the 2D radial dam break on a 64 x 64 structured
-triangulation of [-1, 1]^2 (8192 triangles), order p = 2, inner disc r < 0.3
-depth 2.0, outer depth 0.5, flat bed, yield stress swept over {0, 0.02, 0.1}
-for each of the paper's three regularizations (gamma = beta = 1e3), eta = 0.01:
-nine instances.  One benchmark step advances every instance by ``--inner``
-CFL-limited SSP-RK3 steps (each step = 3 x (E-step, face flux, volume/lift/
-mass-solve/update) + FP64 step-size reduction).  The L2 cache is flushed
+Workload (default): the large 2D Bingham slump on a 2048 x 2048 structured
+triangulation of [-1, 1]^2 (8,388,608 triangles), order p = 2, Gaussian
+mound of depth 1 (sigma 0.15) on a plane of slope 0.05 with a 16-mode seeded
+bed of amplitude 0.05, bi-viscosity regularization (yield stress 0.05,
+gamma = 1e3, eta = 0.01), in FP64.  One benchmark step advances the state by
+``--inner`` CFL-limited SSP-RK3 steps (each step = 3 x (E-step, face flux,
+volume/lift/mass-solve/update) + FP64 step-size reduction).  The same
+workload then runs in FP32 (FP64 step-size and mass reductions) and is
+reported under "mixed", with its relative L2 distance from the FP64 run at
+full size and from the FP64 oracle on a sample.  The L2 cache is flushed
 (256 MiB write) before every timed step, outside the timed events.
 
 Metric: DOF-updates/s = elements x nodes x fields x RK3 steps / time (the
 auxiliary E is not counted), summed over all instances and all ranks.
 
+Other workloads (--workload): the 9-instance radial dam-break sweep, the 1D
+dam break, the bump dam break, the 256-instance ensemble, the paper's 1D
+implicit dam break and a 2D backward-Euler Newton-Krylov run.
 ``--impl reference`` times the FP64 CPU oracle instead (see ``oracle/``).
 """
 import argparse
@@ -39,7 +45,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="radial",
+    ap.add_argument("--workload", default="slump",
                     choices=["radial", "dam1d", "bump", "ensemble", "slump", "implicit_dam", "newton2d"],
                     help="radial: 9-instance radial dam-break sweep (64x64x2, p=2); dam1d: 1D dam break "
                          "(200 el, p=1); bump: dam break over a bump (512x512x2 jittered, p=3); ensemble: "
@@ -61,6 +67,10 @@ def parse():
                          "dg_batch_set_tiles) instead of the autotuner's choice; for profiling")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="slump in FP64: skip the FP32 companion run reported under 'mixed'")
+    ap.add_argument("--compare-steps", type=int, default=10,
+                    help="slump in FP64: steps of the full-size FP64-vs-FP32 comparison")
     ap.add_argument("--oracle-worker", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--oracle-seconds", type=float, default=15.0)
     a = ap.parse_args()
@@ -79,7 +89,7 @@ WORKLOAD_DEFAULTS = {
     "dam1d": dict(precision="fp64", inner=100),
     "bump": dict(precision="fp32", inner=10),
     "ensemble": dict(precision="fp32", inner=10),
-    "slump": dict(precision="fp32", inner=5),
+    "slump": dict(precision="fp64", inner=1),
     "implicit_dam": dict(precision="fp64", inner=200),
     "newton2d": dict(precision="fp64", inner=2),
 }
@@ -246,12 +256,11 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-# FP64 and FP32 pipe peaks derived from unit counts and the maximum SM clock:
-# 152 SMs x 2070 MHz x 2 flop/FMA x lanes/SM/clk (FP32: 128; FP64: 2 on GB300,
-# the nominal 1.25 TFLOP/s of the part).
-SM_COUNT, SM_MAX_MHZ = 152, 2070.0
-FP32_PEAK_TFLOPS = SM_COUNT * SM_MAX_MHZ * 1e6 * 2 * 128 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+# FP64 and FP32 pipe peaks are derived from unit counts and the maximum SM
+# clock (SMs x 2070 MHz x 2 flop/FMA x FMA lanes/SM/clk: FP32 128, FP64 2 on
+# GB300, whose nominal FP64 rate is 1.25 TFLOP/s) and measured beside that by
+# the library's FMA probe (include/dg_probe.h).
+SM_MAX_MHZ = 2070.0
 
 
 def traffic_record(kernel, workload):
@@ -559,34 +568,26 @@ def newton_main(args):
 
 # ---------------------------------------------------------------- GPU leg
 
-def main():
-    args = parse()
-    if args.oracle_worker:
-        oracle_worker(args.oracle_worker)
-        return
-    if args.impl == "reference":
-        reference_main(args)
-        return
+def pipe_peaks(G, stream):
+    """FP64 and FP32 pipe peaks (TFLOP/s): derived from the unit counts and
+    the maximum SM clock, and measured live by the library's FMA probe."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    derived = {"fp64": sms * SM_MAX_MHZ * 1e6 * 2 * 2 / 1e12, "fp32": sms * SM_MAX_MHZ * 1e6 * 2 * 128 / 1e12}
+    probe = {"fp64": G.fma_rate(G.PREC_FP64, stream=stream) / 1e12,
+             "fp32": G.fma_rate(G.PREC_FP32, stream=stream) / 1e12}
+    return derived, probe, sms
+
+
+def measure(args, G, cases, prec, stream, flush, world, local, clocks=True, e2e_on=True, compare_steps=0):
+    """Builds the workload at one precision, times ``args.steps`` bench steps
+    (after ``args.warmup``), times the dominant kernel on its own launching
+    stream and (optionally) the end-to-end path with host buffers.  With
+    compare_steps > 0 it finally resets every instance to its initial state,
+    runs that many steps and returns instance 0's state (a CUDA tensor)."""
     import numpy as np
     import torch
     import torch.distributed as dist
-    import paper_2301_11238_gb300 as G
-    if args.workload == "implicit_dam":
-        implicit_main(args)
-        return
-    if args.workload == "newton2d":
-        newton_main(args)
-        return
-
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    if world > 1:
-        dist.init_process_group("nccl")
-    prec = G.PREC_FP64 if args.precision == "fp64" else G.PREC_FP32
-    stream = torch.cuda.Stream()
-    cases = workload_cases(args)
     batch, solvers, V0s, tiles = None, [], [], None
     with torch.cuda.stream(stream):
         if args.mode == "batch":
@@ -606,7 +607,6 @@ def main():
             units_per_inner = sum(s.K * s.Np * s.nV for s in solvers)
             launches_per_step = sum(s.launches_per_step() for s in solvers) * args.inner
     units_per_step = units_per_inner * args.inner
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def barrier():
         if world > 1:
@@ -620,6 +620,16 @@ def main():
             for s in solvers:
                 s.advance(args.inner)
 
+    class _NoClock:
+        def __enter__(self):
+            return self
+
+        def __exit__(self, *a):
+            pass
+
+        def summary(self):
+            return None
+
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             one_step()
@@ -627,7 +637,7 @@ def main():
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(args.steps)]
         barrier()
-        with ClockSampler(local) as clk:
+        with (ClockSampler(local) if clocks else _NoClock()) as clk:
             for k in range(args.steps):
                 flush.zero_()
                 evs[k][0].record(stream)
@@ -658,30 +668,10 @@ def main():
         else:
             kt = solvers[min(3, len(solvers) - 1)].time_kernels(20)
             dim, p, K = cases[0].dim, cases[0].order, solvers[min(3, len(solvers) - 1)].K
-    vol_ms = kt["volume"]
-    flops = volume_flops(dim, p) * K
-    rs = 8 if prec == G.PREC_FP64 else 4
-    peak_tf = FP64_PEAK_TFLOPS if prec == G.PREC_FP64 else FP32_PEAK_TFLOPS
-    achieved_tf = flops / (vol_ms * 1e-3) / 1e12
-    pk, pk_kind = peaks()
-    vbytes = volume_bytes(dim, p, rs) * K
-    wl_key = f"{args.workload}_{args.mode}_{args.precision}"
-    roof = {"bound": "alu", "kernel": f"volume_kernel<{dim},{p},{'double' if rs == 8 else 'float'},"
-                                      f"{'true' if batch is not None else 'false'}>",
-            "achieved": achieved_tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": achieved_tf / peak_tf,
-            "peak_source": ("FP64 pipe: 152 SMs x 2070 MHz x 2 flop x 2 DFMA/clk/SM = 1.26 TFLOP/s "
-                            "(nominal 1.25; 1.255 measured by an FMA probe)"
-                            if rs == 8 else "FP32 pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz"),
-            "traffic": traffic_record("volume_kernel", wl_key),
-            "elements_per_launch": K,
-            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": vbytes,
-            "hbm_gbs_at_algorithmic_bytes": vbytes / (vol_ms * 1e-3) / 1e9,
-            "hbm_frac": vbytes / (vol_ms * 1e-3) / 1e9 / pk["hbm_gbs"], "hbm_peak_source": pk_kind,
-            "kernel_ms": kt}
 
     # ---- end to end through the public API with host buffers
     e2e = None
-    if not args.no_e2e:
+    if e2e_on:
         pinned = [torch.from_numpy(np.ascontiguousarray(v)).pin_memory() for v in V0s]
         out_host = [torch.empty_like(x).pin_memory() for x in pinned]
         dev = [torch.empty_like(x, device="cuda") for x in pinned]
@@ -699,11 +689,7 @@ def main():
                         batch.set_state(i, dev[i])
                     else:
                         solvers[i].set_state(dev[i])
-                if batch is not None:
-                    batch.advance(args.inner)
-                else:
-                    for s in solvers:
-                        s.advance(args.inner)
+                one_step()
                 for i in range(len(V0s)):
                     if batch is not None:
                         batch.get_state_device(i, dev[i])
@@ -713,11 +699,134 @@ def main():
                 ev[k][1].record(stream)
             stream.synchronize()
             barrier()
-        e_ms = sum(a.elapsed_time(b) for a, b in ev)
+        e_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev), device="cuda")
         e2e = {"value": units_per_step * args.steps * world / (e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d,
                "note": "per step: pinned host->device copy of every instance's state, set_state, "
                        "advance, get_state, device->host copy"}
+        del pinned, out_host, dev
+
+    final = None
+    if compare_steps > 0:
+        with torch.cuda.stream(stream):
+            for i, v in enumerate(V0s):
+                if batch is not None:
+                    batch.set_state(i, v)
+                else:
+                    solvers[i].set_state(v)
+            if batch is not None:
+                batch.run(compare_steps)
+                final = torch.empty(batch.shapes[0], dtype=torch.float64, device="cuda")
+                batch.get_state_device(0, final)
+            else:
+                solvers[0].run(compare_steps)
+                final = torch.empty((solvers[0].nV, solvers[0].K, solvers[0].Np), dtype=torch.float64,
+                                    device="cuda")
+                solvers[0].get_state_device(final)
+            stream.synchronize()
+    for s in solvers:
+        s.close()
+    if batch is not None:
+        batch.close()
+    return dict(value=value, total_ms=total_ms, stats=stats, kt=kt, dim=dim, p=p, K=K, tiles=tiles,
+                e2e=e2e, clk=clk.summary(), launches=launches_per_step * args.steps, n_inst=len(V0s),
+                final=final)
+
+
+def roofline(r, prec, G, args, peaks_derived, peaks_probe, batch_mode):
+    """Roofline object of the dominant (volume) kernel: the FP64 or FP32
+    pipe at algorithmic flops, with HBM at algorithmic bytes beside it."""
+    dim, p, K, kt = r["dim"], r["p"], r["K"], r["kt"]
+    vol_ms = kt["volume"]
+    rs = 8 if prec == G.PREC_FP64 else 4
+    key = "fp64" if rs == 8 else "fp32"
+    flops = volume_flops(dim, p) * K
+    achieved_tf = flops / (vol_ms * 1e-3) / 1e12
+    pk, pk_kind = peaks()
+    vbytes = volume_bytes(dim, p, rs) * K
+    peak = peaks_derived[key]
+    wl_key = f"{args.workload}_{args.mode}_{'fp64' if rs == 8 else 'fp32'}"
+    return {"bound": "alu", "kernel": f"volume_kernel<{dim},{p},{'double' if rs == 8 else 'float'},"
+                                      f"{'true' if batch_mode else 'false'}>",
+            "achieved": achieved_tf, "peak": peak, "unit": "TFLOP/s", "frac": achieved_tf / peak,
+            "peak_source": (f"{'FP64' if rs == 8 else 'FP32'} pipe from unit counts: SMs x "
+                            f"{2 if rs == 8 else 128} FMA lanes/SM/clk x 2 flop x {SM_MAX_MHZ:g} MHz"),
+            "peak_probe": peaks_probe[key], "frac_of_probe": achieved_tf / peaks_probe[key],
+            "traffic": traffic_record("volume_kernel", wl_key),
+            "elements_per_launch": K,
+            "algorithmic_flops_per_launch": flops, "algorithmic_bytes_per_launch": vbytes,
+            "hbm_gbs_at_algorithmic_bytes": vbytes / (vol_ms * 1e-3) / 1e9,
+            "hbm_frac": vbytes / (vol_ms * 1e-3) / 1e9 / pk["hbm_gbs"], "hbm_peak_source": pk_kind,
+            "kernel_ms": kt}
+
+
+def accuracy_vs_oracle(args, G, prec, stream, res, sdesc, sc):
+    import numpy as np
+    import torch
+    with torch.cuda.stream(stream):
+        s_acc, _, _ = G.solver_from_case(sc, precision=prec, stream=stream)
+        s_acc.run(res["steps"])
+        Vg = s_acc.get_state(with_E=False)
+        s_acc.close()
+    Vo = np.asarray(res["final"])
+    return {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
+            "after_steps": res["steps"], "case": sdesc,
+            "precision": "fp64" if prec == G.PREC_FP64 else "fp32",
+            "sigma0": sc.params["sigma0"], "regularization": sc.params["reg"]}
+
+
+def main():
+    args = parse()
+    if args.oracle_worker:
+        oracle_worker(args.oracle_worker)
+        return
+    if args.impl == "reference":
+        reference_main(args)
+        return
+    import torch
+    import torch.distributed as dist
+    import paper_2301_11238_gb300 as G
+    if args.workload == "implicit_dam":
+        implicit_main(args)
+        return
+    if args.workload == "newton2d":
+        newton_main(args)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    prec = G.PREC_FP64 if args.precision == "fp64" else G.PREC_FP32
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    peaks_derived, peaks_probe, sms = pipe_peaks(G, stream)
+    cases = workload_cases(args)
+    # the mixed-precision companion run of the FP64 headline (same mesh and
+    # physics in FP32) and the full-size FP64-vs-FP32 comparison
+    mixed_on = args.precision == "fp64" and args.workload == "slump" and not args.no_mixed
+    cmp_steps = args.compare_steps if mixed_on else 0
+    r = measure(args, G, cases, prec, stream, flush, world, local, e2e_on=not args.no_e2e,
+                compare_steps=cmp_steps)
+    roof = roofline(r, prec, G, args, peaks_derived, peaks_probe, args.mode == "batch")
+    final64 = r.pop("final")
+
+    mixed = None
+    if mixed_on:
+        r32 = measure(args, G, cases, G.PREC_FP32, stream, flush, world, local, clocks=True,
+                      e2e_on=not args.no_e2e, compare_steps=cmp_steps)
+        final32 = r32.pop("final")
+        diff = float(torch.linalg.vector_norm(final32 - final64) / torch.linalg.vector_norm(final64))
+        del final32
+        mixed = {"precision": "fp32 state and arithmetic; FP64 step-size and mass reductions",
+                 "value": r32["value"], "unit": UNIT, "ms_per_step": r32["total_ms"] / args.steps,
+                 "speedup_vs_fp64": r32["value"] / r["value"],
+                 "roofline": roofline(r32, G.PREC_FP32, G, args, peaks_derived, peaks_probe, args.mode == "batch"),
+                 "e2e": r32["e2e"], "gpu_launches": r32["launches"], "clocks": r32["clk"], "tiles": r32["tiles"],
+                 "rel_l2_vs_gpu_fp64_full_size": diff, "compare_steps": cmp_steps}
+    del final64
 
     # ---- accuracy and CPU baseline (rank 0, N=1 only)
     cpu = None
@@ -729,35 +838,29 @@ def main():
         cpu = {"value": res["units_per_step"] * res["steps"] / res["seconds"], "unit": UNIT, "cores": 1,
                "kind": "oracle",
                "sample": f"{res['steps']} SSP-RK3 steps of {sdesc}, {res['seconds']:.1f} s on one host core"}
-        with torch.cuda.stream(stream):
-            s_acc, _, _ = G.solver_from_case(sc, precision=prec, stream=stream)
-            s_acc.run(res["steps"])
-            Vg = s_acc.get_state(with_E=False)
-            s_acc.close()
-        Vo = np.asarray(res["final"])
-        acc = {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
-               "after_steps": res["steps"], "case": sdesc, "precision": args.precision}
+        acc = accuracy_vs_oracle(args, G, prec, stream, res, sdesc, sc)
+        if mixed is not None:
+            mixed["accuracy"] = accuracy_vs_oracle(args, G, G.PREC_FP32, stream, res, sdesc, sc)
 
+    stats = r["stats"]
     dt_info = ({f"sigma0={c.params['sigma0']},reg={c.params['reg']}": st["dt_last"]
                 for c, st in zip(cases, stats)} if len(cases) <= 16 else
                {"min": min(st["dt_last"] for st in stats), "max": max(st["dt_last"] for st in stats)})
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if rs == 8 else "f32",
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["total_ms"] / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == G.PREC_FP64 else "f32",
             "data": "synthetic",
-            "config": {"workload": workload_name(args), "instances": len(V0s),
+            "config": {"workload": workload_name(args), "instances": r["n_inst"],
                        "elements_total": int(sum(c.etov.shape[0] for c in cases)), "mode": args.mode,
-                       "tiles": tiles,
+                       "tiles": r["tiles"],
                        "inner_rk3_steps_per_step": args.inner, "l2": "flushed (256 MiB write) before each step",
-                       "parallelism": f"replicas x{world}", "dt_last": dt_info},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
-            "clocks": clk.summary(), "accuracy": acc}
+                       "parallelism": f"replicas x{world}", "dt_last": dt_info,
+                       "simulated_time_per_step": {k: v * args.inner for k, v in dt_info.items()},
+                       "sms": sms},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": r["e2e"], "gpu_launches": r["launches"],
+            "clocks": r["clk"], "accuracy": acc, "mixed": mixed}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    for s in solvers:
-        s.close()
-    if batch is not None:
-        batch.close()
     if world > 1:
         dist.destroy_process_group()
 

@@ -224,6 +224,9 @@ dg_status dg_swe_sync(dg_swe_ctx *ctx, dg_swe_stats *stats);
  * cudaFree or allocating library routine).
  *  - Problems whose scratch need (dg_swe_static_scratch_need) exceeds the
  *    array are rejected with DG_ERR_ARG and a message giving both sizes.
+ *  - Call it with the context's device current (the device that was current
+ *    at dg_swe_set_workspace); with another device current it returns
+ *    DG_ERR_ARG, since the array it would use belongs to that other device.
  *  - The first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) for that device; make that first call before any
  *    CUDA stream capture.

@@ -241,6 +241,21 @@ def _stats_dict(st):
                 mass=st.mass, mass0=st.mass0, status=st.status)
 
 
+def fma_rate(precision=PREC_FP64, repeats=5, stream=None):
+    """Measured fused multiply-add rate (flop/s, FMA = 2) of the current
+    GPU's FP64 or FP32 pipe (include/dg_probe.h)."""
+    torch = _torch()
+    L = _lib.lib()
+    scratch = torch.empty(int(L.dg_probe_scratch_bytes()), dtype=torch.uint8, device="cuda")
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double()
+    st = L.dg_probe_fma_rate(int(precision), int(repeats), C.c_void_p(scratch.data_ptr()),
+                             C.c_void_p(s.cuda_stream), C.byref(out))
+    if st != DG_OK:
+        raise DGError(st, "dg_probe_fma_rate failed")
+    return out.value
+
+
 def solver_from_case(case, precision=PREC_FP64, order=None, with_state=True, stream=None):
     """Build a Solver for a synthetic case; sets the initial state sampled at
     the library's own node coordinates."""

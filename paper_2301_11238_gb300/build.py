@@ -18,7 +18,7 @@ LIB = os.path.join(BUILD, "libdgswe.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-O3", "--expt-relaxed-constexpr"]
-SOURCES = ["dg_swe.cu", "dg_host.cpp", "dg_implicit.cu", "dg_batch.cu", "dg_newton.cu"]
+SOURCES = ["dg_swe.cu", "dg_host.cpp", "dg_implicit.cu", "dg_batch.cu", "dg_newton.cu", "dg_probe.cu"]
 
 
 def _nvcc():

@@ -47,6 +47,7 @@ struct dg_swe_ctx {
   std::vector<double> bed;
   bool has_bed = false;
   size_t rsize = 8;
+  int device = -1;  // device current at dg_swe_set_workspace (the workspace's device)
   // workspace
   size_t ws_need = 0;
   char* ws = nullptr;

@@ -360,6 +360,10 @@ dg_status dg_swe_set_workspace(dg_swe_ctx* c, void* ptr, size_t bytes) {
   if (!ptr || bytes < c->ws_need) return fail(c, DG_ERR_WORKSPACE, "workspace missing or smaller than dg_swe_workspace_size()");
   if (((uintptr_t)ptr & 255) != 0) return fail(c, DG_ERR_WORKSPACE, "workspace must be 256-byte aligned");
   destroy_graphs(c);
+  {
+    const cudaError_t e = cudaGetDevice(&c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+  }
   c->ws = (char*)ptr;
   const int64_t K = c->mesh.K, F = c->mesh.F;
   const int nf = c->dim + 1;
@@ -647,12 +651,15 @@ constexpr int kMaxDevices = 64;
 std::mutex g_static_mu;
 void* g_static_ptr[kMaxDevices] = {};
 
-// Device address of g_static_scratch on the current device (looked up on the
-// first call per device).
+// Device address of g_static_scratch on the context's device, which must be
+// the current device (looked up on the first call per device).
 dg_status static_scratch(dg_swe_ctx* c, void** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaGetDevice");
+  if (dev != c->device)
+    return fail(c, DG_ERR_ARG, "device " + std::to_string(dev) + " is current but the context's workspace is on device " +
+                                   std::to_string(c->device) + "; make the context's device current");
   if (dev < 0 || dev >= kMaxDevices) return fail(c, DG_ERR_UNSUPPORTED, "device ordinal beyond 63");
   std::lock_guard<std::mutex> lk(g_static_mu);
   if (!g_static_ptr[dev]) {

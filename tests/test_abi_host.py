@@ -103,3 +103,14 @@ def test_empty_mesh_rejected():
     with pytest.raises(G.DGError) as ei:
         G.Solver(1, coords, np.zeros((0, 2), dtype=np.int32), 1, 0, synth.cases.default_params(), allocate=False)
     assert ei.value.status == G.DG_ERR_ARG
+
+
+def test_fma_probe_rejects_bad_arguments():
+    import paper_2301_11238_gb300._lib as L
+    lib = L.lib()
+    out = C.c_double()
+    fake = C.c_void_p(0x1000)  # never dereferenced: the arguments are rejected first
+    assert lib.dg_probe_fma_rate(7, 5, fake, None, C.byref(out)) == L.DG_ERR_ARG
+    assert lib.dg_probe_fma_rate(0, 0, fake, None, C.byref(out)) == L.DG_ERR_ARG
+    assert lib.dg_probe_fma_rate(0, 5, None, None, C.byref(out)) == L.DG_ERR_ARG
+    assert lib.dg_probe_fma_rate(0, 5, fake, None, None) == L.DG_ERR_ARG

@@ -145,3 +145,36 @@ def test_staged_volume_rejects_oversized_tile():
     B.set_tiles([[t[0], t[1], -32]])
     B.run(2)
     B.close()
+
+
+def test_batch_mass_multiblock_instances():
+    """Mass and initial mass of instances that span several 256-element
+    reduction blocks (with ragged last blocks), next to small ones: equal to
+    the single-context solver and to the oracle's integral of h of the same
+    state to 1e-14, and reproducible bit for bit across stats calls."""
+    import paper_2301_11238_gb300 as G
+    cases = [synth.dam_break_1d(n_el=3001, order=2),
+             synth.radial_dam_2d(n=4, order=1),
+             synth.radial_dam_2d(n=40, order=2, reg=3, sigma0=0.02, gamma=50.0),
+             synth.dam_break_1d(n_el=50, order=1),
+             synth.radial_dam_2d(n=37, order=3)]
+    B, V0s = G.batch_from_cases(cases)
+    discs = [oracle_build(c)[0] for c in cases]
+    st0 = B.stats()
+    for i, d in enumerate(discs):
+        m_ref = d.total_mass(d.to_modal(V0s[i]))
+        assert abs(st0[i]["mass0"] - m_ref) <= 1e-14 * abs(m_ref), (i, st0[i]["mass0"], m_ref)
+        assert abs(st0[i]["mass"] - m_ref) <= 1e-14 * abs(m_ref)
+    st = B.run(4)
+    again = B.stats()
+    for i, (c, d) in enumerate(zip(cases, discs)):
+        VB = B.get_state(i)
+        m_ref = d.total_mass(d.to_modal(VB))
+        assert abs(st[i]["mass"] - m_ref) <= 1e-14 * abs(m_ref), (i, st[i]["mass"], m_ref)
+        assert st[i]["mass"] == again[i]["mass"] and st[i]["mass0"] == again[i]["mass0"]
+        s, _, _ = G.solver_from_case(c)
+        ss = s.run(4)
+        assert abs(ss["mass"] - st[i]["mass"]) <= 1e-14 * abs(ss["mass"])
+        assert abs(ss["mass0"] - st[i]["mass0"]) <= 1e-14 * abs(ss["mass0"])
+        s.close()
+    B.close()

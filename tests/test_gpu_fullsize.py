@@ -1,6 +1,6 @@
 """Parity at the benchmark's full sizes, in the launch configuration bench.py
 times (one batch, autotuned kernel forms, CUDA-graph replay): one SSP-RK3
-step of the 8.4M-triangle slump (FP32), the 524,288-triangle bump dam break
+step of the 8.4M-triangle slump (FP64 and FP32), the 524,288-triangle bump dam break
 (p = 3, FP32) and the nine-instance radial sweep (FP64), checked on sampled
 elements against the oracle, and whole instances of the 256-instance
 ensemble (FP32).
@@ -135,3 +135,10 @@ def test_ensemble_full_size_fp32_whole_instances():
         V1o, _ = d.ssp_rk3_step(d.to_modal(np.asarray(V0s[i])), stats[i]["dt_last"])
         assert rel_l2(B.get_state(i), d.to_nodal(V1o)) < 1e-5, i
     B.close()
+
+
+def test_slump_full_size_fp64_sampled():
+    """The benchmark's headline: 8,388,608 triangles, p = 2, FP64, one step
+    in the benchmark's launch configuration; 12 sampled elements at the FP64
+    tolerance."""
+    _sampled_check(synth.slump_2d(n=2048), 0, 12, 1e-12, seed=1)
