@@ -54,7 +54,8 @@ def parse():
                          "newton2d: 2D radial dam break (64x64x2, p=2) with backward Euler + Newton-Krylov")
     ap.add_argument("--solver", default="mixed", choices=["fp64", "mixed"],
                     help="implicit_dam: FP64 block Thomas, or FP32 factorization + FP64 refinement")
-    ap.add_argument("--precision", default=None, choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp32tc"],
+                    help="fp32tc: FP32 with the p >= 2 triangle volume contractions on the tensor cores")
     ap.add_argument("--mode", default="batch", choices=["batch", "solo"],
                     help="batch: all instances in one dg_batch (one launch per phase); solo: one context each")
     ap.add_argument("--inner", type=int, default=None, help="RK3 steps per instance per bench step")
@@ -745,9 +746,11 @@ def roofline(r, prec, G, args, peaks_derived, peaks_probe, batch_mode):
     pk, pk_kind = peaks()
     vbytes = volume_bytes(dim, p, rs) * K
     peak = peaks_derived[key]
-    wl_key = f"{args.workload}_{args.mode}_{'fp64' if rs == 8 else 'fp32'}"
-    return {"bound": "alu", "kernel": f"volume_kernel<{dim},{p},{'double' if rs == 8 else 'float'},"
-                                      f"{'true' if batch_mode else 'false'}>",
+    tcf = prec == G.PREC_FP32_TC and dim == 2 and p >= 2
+    wl_key = f"{args.workload}_{args.mode}_{'fp64' if rs == 8 else ('fp32tc' if tcf else 'fp32')}"
+    kname = (f"volume_tc_kernel<{p},{'true' if batch_mode else 'false'}>" if tcf else
+             f"volume_kernel<{dim},{p},{'double' if rs == 8 else 'float'},{'true' if batch_mode else 'false'}>")
+    return {"bound": "alu", "kernel": kname,
             "achieved": achieved_tf, "peak": peak, "unit": "TFLOP/s", "frac": achieved_tf / peak,
             "peak_source": (f"{'FP64' if rs == 8 else 'FP32'} pipe from unit counts: SMs x "
                             f"{2 if rs == 8 else 128} FMA lanes/SM/clk x 2 flop x {SM_MAX_MHZ:g} MHz"),
@@ -771,7 +774,7 @@ def accuracy_vs_oracle(args, G, prec, stream, res, sdesc, sc):
     Vo = np.asarray(res["final"])
     return {"rel_l2_vs_fp64_oracle": float(np.linalg.norm(Vg - Vo) / np.linalg.norm(Vo)),
             "after_steps": res["steps"], "case": sdesc,
-            "precision": "fp64" if prec == G.PREC_FP64 else "fp32",
+            "precision": {G.PREC_FP64: "fp64", G.PREC_FP32: "fp32", G.PREC_FP32_TC: "fp32tc"}[prec],
             "sigma0": sc.params["sigma0"], "regularization": sc.params["reg"]}
 
 
@@ -799,10 +802,9 @@ def main():
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
-    prec = G.PREC_FP64 if args.precision == "fp64" else G.PREC_FP32
+    prec = {"fp64": G.PREC_FP64, "fp32": G.PREC_FP32, "fp32tc": G.PREC_FP32_TC}[args.precision]
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    peaks_derived, peaks_probe, sms = pipe_peaks(G, stream)
     cases = workload_cases(args)
     # the mixed-precision companion run of the FP64 headline (same mesh and
     # physics in FP32) and the full-size FP64-vs-FP32 comparison
@@ -810,6 +812,8 @@ def main():
     cmp_steps = args.compare_steps if mixed_on else 0
     r = measure(args, G, cases, prec, stream, flush, world, local, e2e_on=not args.no_e2e,
                 compare_steps=cmp_steps)
+    # pipe peaks measured right after the timed work, with the GPU's clocks up
+    peaks_derived, peaks_probe, sms = pipe_peaks(G, stream)
     roof = roofline(r, prec, G, args, peaks_derived, peaks_probe, args.mode == "batch")
     final64 = r.pop("final")
 

@@ -19,7 +19,7 @@ extern "C" {
 
 /* Times a kernel of independent fused multiply-add chains (8 chains per
  * thread, 8 blocks of 256 threads per SM of the current device) on `stream`
- * (a cudaStream_t, NULL for the legacy default stream): one untimed launch,
+ * (a cudaStream_t, NULL for the legacy default stream): five untimed launches,
  * then `repeats` launches timed together with CUDA events on that stream.
  *  precision: DG_PREC_FP64 or DG_PREC_FP32.
  *  repeats:   1 .. 1000.

@@ -73,7 +73,18 @@ enum { DG_REG_NONE = 0,       /* Newtonian: sigma_B = 0                         
        DG_REG_BIVISC = 5 };   /* min(2 gamma |E|, 2 sigma0) sign E  (bi-viscosity)      */
 
 enum { DG_PREC_FP64 = 0,     /* state, fluxes and contractions in FP64                  */
-       DG_PREC_FP32 = 1 };   /* FP32 state and arithmetic; FP64 CFL and mass reductions */
+       DG_PREC_FP32 = 1,     /* FP32 state and arithmetic; FP64 CFL and mass reductions */
+       DG_PREC_FP32_TC = 2 };/* as DG_PREC_FP32, but on triangles of order 2 and 3 the
+                                volume pass runs its three dense contractions (the
+                                interpolation of the nodal fields to the volume points,
+                                the test-function contraction of the pointwise fluxes of
+                                Eq. WeakForm51 and the h-weighted mass matrix of the
+                                primitive-variable time term, Appendix A) on the tensor
+                                cores (tcgen05, TF32 operands split into high and low
+                                parts, FP32 accumulation; about 22 significant bits per
+                                operand against FP32's 24).  Elsewhere (1D, order 1) it equals
+                                DG_PREC_FP32.  Results differ from DG_PREC_FP32 by
+                                rounding only.                                           */
 
 typedef struct {
   int32_t mode[7];   /* per slot: V fields (h, u_1[, u_2]) then E fields     */

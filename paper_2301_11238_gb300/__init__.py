@@ -13,7 +13,7 @@ from . import _lib
 from ._lib import (DG_OK, DG_ERR_ARG, DG_ERR_CUDA, DG_ERR_WORKSPACE, DG_ERR_NONFINITE,  # noqa: F401
                    DG_ERR_NEWTON, DG_ERR_UNSUPPORTED, DG_ERR_TIMEOUT, STATUS_NAMES)
 
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32_TC = 0, 1, 2
 
 
 class DGError(RuntimeError):

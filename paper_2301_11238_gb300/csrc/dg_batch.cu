@@ -12,6 +12,7 @@
 #include "../../include/dg_batch.h"
 #include "dg_ctx.h"
 #include "dg_kernels.cuh"
+#include "dg_tc.cuh"
 
 using namespace dgswe;
 
@@ -47,7 +48,7 @@ struct Group {
   std::vector<int64_t> ebeg;
   struct {
     size_t geo, nbr, nbrf, fid, fn, fsj, fe1, fe2, ff1, ff2, fnrm, fsjf, bed, inst, ebeg, gid, V[3], E, wflux, wint,
-        blk_e, blk_gid, mblk, partial;
+        blk_e, blk_gid, mblk, partial, tcimg;
   } off{};
   std::vector<int64_t> blk_e;      // step-size blocks: element ranges (n_blk + 1)
   std::vector<int32_t> blk_gid;    // global instance of each block
@@ -145,15 +146,23 @@ static __global__ void mass_members_kernel(int first, int count, const int32_t* 
 template <int DIM, int P, typename R>
 struct GDrv final : GroupDrv {
   using S = Sh<DIM, P>;
+  // the tensor-core volume form exists for FP32 triangles of order >= 2
+  static constexpr bool kTcForm = DIM == 2 && P >= 2 && sizeof(R) == 4;
   EstepOps<DIM, P, R> eo{};
   FaceOps<DIM, P, R> fo{};
   VolOps<DIM, P, R> vo{};
+  bool tc = false;
+  std::unique_ptr<tc::Launcher<(P >= 2 ? P : 2), true>> tcl;
   int n_sm = 0;
   size_t smem_optin = 0;     // shared memory a block may use (static + dynamic)
   size_t staged_static = 0;  // the staged kernel's static shared memory
   std::map<int, int> staged_grid;  // staged volume block size -> persistent grid size (0: not launchable)
-  explicit GDrv(const RefOps& o) {
+  explicit GDrv(const RefOps& o, bool use_tc) {
     fill_ops<DIM, P, R>(o, eo, fo, vo);
+    if constexpr (kTcForm) {
+      tc = use_tc;
+      if (tc) tcl.reset(new tc::Launcher<P, true>());
+    }
     int dev = 0, v = 0;
     if (cudaGetDevice(&dev) == cudaSuccess) {
       if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess) n_sm = v;
@@ -214,6 +223,15 @@ struct GDrv final : GroupDrv {
   }
   void volume(dg_batch* b, Group& g, int vin, int vout, double c0, double c1, cudaStream_t s) override {
     const int K = (int)g.K, F = (int)g.F;
+    if constexpr (kTcForm) {
+      if (tc) {  // the tensor-core form has its own fixed launch shape; the tile setting is not used
+        (*tcl)(K, F, b->at<float>(g.off.V[vin]), b->at<float>(g.off.V[0]), b->at<float>(g.off.V[vout]),
+               b->at<float>(g.off.E), g.has_bed ? b->at<float>(g.off.bed) : nullptr, b->at<float>(g.off.geo),
+               b->at<int32_t>(g.off.fid), b->at<float>(g.off.wflux), vo, b->at<float>(g.off.tcimg), Phys<float>{},
+               ptab(b), b->at<int32_t>(g.off.inst), 1, (float)c0, (float)c1, b->at<DevScalars>(b->off_sc), s);
+        return;
+      }
+    }
     if (g.tile[2] < 0) {
       const int T = -g.tile[2];
       const int ntiles = (K + T - 1) / T;
@@ -257,9 +275,9 @@ struct GDrv final : GroupDrv {
 };
 
 template <typename R>
-std::unique_ptr<GroupDrv> make_gdrv(int dim, int p, const RefOps& o) {
+std::unique_ptr<GroupDrv> make_gdrv(int dim, int p, const RefOps& o, bool use_tc) {
 #define GCASE(D, PP) \
-  if (dim == D && p == PP) return std::unique_ptr<GroupDrv>(new GDrv<D, PP, R>(o));
+  if (dim == D && p == PP) return std::unique_ptr<GroupDrv>(new GDrv<D, PP, R>(o, use_tc));
   GCASE(1, 1) GCASE(1, 2) GCASE(1, 3) GCASE(2, 1) GCASE(2, 2) GCASE(2, 3)
 #undef GCASE
   return nullptr;
@@ -415,7 +433,8 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
       g.dim = c->dim;
       g.p = c->p;
       g.ops = c->ops;
-      g.drv = b->prec == DG_PREC_FP64 ? make_gdrv<double>(g.dim, g.p, g.ops) : make_gdrv<float>(g.dim, g.p, g.ops);
+      g.drv = b->prec == DG_PREC_FP64 ? make_gdrv<double>(g.dim, g.p, g.ops, false)
+                                      : make_gdrv<float>(g.dim, g.p, g.ops, b->prec == DG_PREC_FP32_TC);
     }
     const int gi = gidx[key];
     Group& g = b->groups[gi];
@@ -574,6 +593,7 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
     g.off.blk_gid = take(g.blk_gid.size() * 4);
     g.off.mblk = take(g.mblk.size() * 4);
     g.off.partial = take(g.blk_gid.size() * 8);
+    g.off.tcimg = take(b->prec == DG_PREC_FP32_TC ? tc::image_bytes(g.dim, g.p) : 0);
   }
   b->off_ptab = take(phys_bytes.size());
   b->off_bct = take(bc_bytes.size());
@@ -634,6 +654,12 @@ dg_status dg_batch_set_workspace(dg_batch* b, void* ptr, size_t bytes) {
     BK(up(g.off.blk_e, g.blk_e.data(), g.blk_e.size() * 8));
     BK(up(g.off.blk_gid, g.blk_gid.data(), g.blk_gid.size() * 4));
     BK(up(g.off.mblk, g.mblk.data(), g.mblk.size() * 4));
+    if (b->prec == DG_PREC_FP32_TC && tc::image_bytes(g.dim, g.p) > 0) {
+      std::vector<float> img;
+      tc::build_image(g.dim, g.p, g.ops, img);
+      BK(up(g.off.tcimg, img.data(), img.size() * 4));
+      BK(cudaStreamSynchronize(s));
+    }
     BK(cudaMemsetAsync(b->ws + g.off.E, 0, (size_t)g.dim * g.dim * g.K * g.ops.Np * b->rsize, s));
     for (int v = 0; v < 3; ++v)
       BK(cudaMemsetAsync(b->ws + g.off.V[v], 0, (size_t)(g.dim + 1) * g.K * g.ops.Np * b->rsize, s));

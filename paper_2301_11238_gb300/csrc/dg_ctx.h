@@ -53,7 +53,7 @@ struct dg_swe_ctx {
   char* ws = nullptr;
   struct {
     size_t geo, nbr, nbrf, fid, fn, fsj, fe1, fe2, ff1, ff2, fnrm, fsjf, bed, V0, V1, V2, E, wflux, partial, wint, sc,
-        bct;
+        bct, tcimg;
   } off{};
   int nblk_dt = 0, nblk_mass = 0;
   cudaStream_t stream = nullptr;

@@ -10,6 +10,7 @@
 #include "../../include/dg_swe.h"
 #include "dg_ctx.h"
 #include "dg_kernels.cuh"
+#include "dg_tc.cuh"
 
 using namespace dgswe;
 
@@ -81,14 +82,35 @@ std::vector<BCEntry<R>> make_bc_table(const dg_swe_params& p) {
 template <int DIM, int P, typename R>
 struct Impl final : Driver {
   using S = Sh<DIM, P>;
+  // the tensor-core volume form exists for FP32 triangles of order >= 2
+  static constexpr bool kTcForm = DIM == 2 && P >= 2 && sizeof(R) == 4;
   EstepOps<DIM, P, R> eo{};
   FaceOps<DIM, P, R> fo{};
   VolOps<DIM, P, R> vo{};
   Phys<R> ph{};
+  bool tc = false;
+  std::unique_ptr<tc::Launcher<(P >= 2 ? P : 2), false>> tcl;
 
   explicit Impl(const dg_swe_ctx& c) {
     fill_ops<DIM, P, R>(c.ops, eo, fo, vo);
     ph = make_phys<R>(c.prm, c.reg);
+    if constexpr (kTcForm) {
+      tc = c.prec == DG_PREC_FP32_TC;
+      if (tc) tcl.reset(new tc::Launcher<P, false>());
+    }
+  }
+  // the tensor-core volume pass (mode as volume_kernel); false if not used
+  bool volume_tc(dg_swe_ctx* c, const void* Vin, const void* V0, void* out, const void* E, const void* wflux, int mode,
+                 double c0, double c1, cudaStream_t s) {
+    if constexpr (kTcForm) {
+      if (!tc) return false;
+      (*tcl)((int)c->mesh.K, (int)c->mesh.F, (const float*)Vin, (const float*)V0, (float*)out, (const float*)E,
+             c->has_bed ? c->at<float>(c->off.bed) : nullptr, c->at<float>(c->off.geo), c->at<int32_t>(c->off.fid),
+             (const float*)wflux, vo, c->at<float>(c->off.tcimg), ph, nullptr, nullptr, mode, (float)c0, (float)c1,
+             c->at<DevScalars>(c->off.sc), s);
+      return true;
+    }
+    return false;
   }
 
   void estep(dg_swe_ctx* c, const void* V, void* E, cudaStream_t s) override {
@@ -107,6 +129,7 @@ struct Impl final : Driver {
   }
   void volume(dg_swe_ctx* c, const void* Vin, const void* V0, void* out, int mode, double c0, double c1,
               cudaStream_t s) override {
+    if (volume_tc(c, Vin, V0, out, c->ws + c->off.E, c->ws + c->off.wflux, mode, c0, c1, s)) return;
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     volume_kernel<DIM, P, R, false><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
         K, F, (const R*)Vin, (const R*)V0, (R*)out, c->at<R>(c->off.E),
@@ -134,6 +157,7 @@ struct Impl final : Driver {
   }
   void residual_from(dg_swe_ctx* c, const void* V, const void* E, const void* wflux, void* out,
                      cudaStream_t s) override {
+    if (volume_tc(c, V, nullptr, out, E, wflux, 0, 0.0, 0.0, s)) return;
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     volume_kernel<DIM, P, R, false><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
         K, F, (const R*)V, nullptr, (R*)out, (const R*)E, c->has_bed ? c->at<R>(c->off.bed) : nullptr,
@@ -257,7 +281,7 @@ dg_status dg_swe_init(const dg_swe_mesh* mesh, int order, int regularization, co
     return fail(*out, DG_ERR_ARG, "need dim in {1,2}, order in {1,2,3}, 1 <= n_elements < 2^27");
   }
   if (regularization < 0 || regularization > 5 || p.n_bc < 1 || p.n_bc > DG_SWE_MAX_BC ||
-      p.precision < 0 || p.precision > 1 || !(p.g > 0) || !(p.rho > 0) || !(p.cfl > 0) || p.eta < 0 ||
+      p.precision < 0 || p.precision > 2 || !(p.g > 0) || !(p.rho > 0) || !(p.cfl > 0) || p.eta < 0 ||
       p.sigma0 < 0 || !(p.h_floor > 0)) {
     *out = c.release();
     return fail(*out, DG_ERR_ARG, "invalid parameters (regularization, n_bc, precision, g, rho, cfl, eta, sigma0, h_floor)");
@@ -342,6 +366,7 @@ dg_status dg_swe_init(const dg_swe_mesh* mesh, int order, int regularization, co
   c->off.wint = take((size_t)Np * 8);
   c->off.sc = take(sizeof(DevScalars));
   c->off.bct = take((size_t)p.n_bc * (c->rsize == 8 ? sizeof(BCEntry<double>) : sizeof(BCEntry<float>)));
+  c->off.tcimg = take(c->prec == DG_PREC_FP32_TC ? tc::image_bytes(c->dim, c->p) : 0);
   c->ws_need = o;
   *out = c.release();
   return DG_OK;
@@ -399,6 +424,12 @@ dg_status dg_swe_set_workspace(dg_swe_ctx* c, void* ptr, size_t bytes) {
   } else {
     auto t = make_bc_table<float>(c->prm);
     CK(cudaMemcpyAsync(c->ws + c->off.bct, t.data(), t.size() * sizeof(t[0]), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (c->prec == DG_PREC_FP32_TC && tc::image_bytes(c->dim, c->p) > 0) {
+    std::vector<float> img;
+    tc::build_image(c->dim, c->p, c->ops, img);
+    CK(cudaMemcpyAsync(c->ws + c->off.tcimg, img.data(), img.size() * 4, cudaMemcpyHostToDevice, s));
     CK(cudaStreamSynchronize(s));
   }
   CK(cudaMemsetAsync(c->ws + c->off.E, 0, (size_t)c->dim * c->dim * K * c->ops.Np * c->rsize, s));
