@@ -326,6 +326,7 @@ void push_phys(const dg_swe_params& p, int reg, std::vector<char>& out) {
   ph.half_inv_beta = (R)(0.5 / p.beta);
   ph.pap_m = (R)p.pap_m;
   ph.h_floor = (R)p.h_floor;
+  ph.h_dry = (R)(kDryFactor * p.h_floor);
   ph.reg = reg;
   ph.pos = p.positivity ? 1 : 0;
   ph.hb = (p.flow_index != 0.0 && p.flow_index != 1.0) ? 1 : 0;

@@ -47,6 +47,8 @@ template <typename R>
 struct Phys {
   R gc, gs, rho_inv, eta, sigma0, gamma, beta, pap_m, h_floor;
   R half_inv_beta;  // 1 / (2 beta), the half-width of the regularizations 1 and 2 (host-computed)
+  R h_dry;          // FP32 contexts: depth below which an element's mass solve runs in FP64
+                    // (kDryFactor x h_floor)
   R hb_n, hb_floor;  // Herschel-Bulkley flow index and rate floor (dg_swe_params)
   int hb;            // 1: power-law viscous part (flow index != 1)
   int reg;
@@ -644,6 +646,126 @@ __device__ __forceinline__ void mass_solve_element(const R (&Vn)[Sh<DIM, P>::NV]
   }
 }
 
+// Near-dry treatment of FP32 contexts: an element whose smallest nodal depth
+// is below h_dry (kDryFactor x h_floor) assembles and solves its h-weighted
+// mass matrix in FP64 (the depths at the quadrature points, M_h = <psi,
+// max(h, h_floor) psi>, M_u dh/dt, the Cholesky factorization and both
+// triangular solves), from its FP32 nodal values and residual.  There M_h
+// has entries of the size of the floor next to entries a thousand times
+// larger, and FP32 would lose their relative accuracy.  The FP64 solve runs
+// in loops over per-thread local arrays: it is rare (fronts and films only)
+// and must not add registers to the FP32 kernels' common path.  FP64
+// contexts and wet elements take the working-precision solve
+// (mass_solve_element), whose formulas this restates.
+constexpr double kDryFactor = 1000.0;
+
+template <int DIM, int P>
+__device__ __forceinline__ void mass_solve_dry(const float (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                               const float (&r)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                               const VolOps<DIM, P, float>& ops, float h_floor, float Jinv,
+                                               float (&dVout)[Sh<DIM, P>::NV][Sh<DIM, P>::NP]) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NQ = S::NQ, NV = S::NV;
+  double V[NV * NP], dV[NV * NP], Mh[NP * NP], rhs[DIM * NP], dinv[NP], y[NP];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) V[v * NP + a] = (double)Vn[v][a];
+  const double jinv = (double)Jinv, hf = (double)h_floor;
+#pragma unroll 1
+  for (int a = 0; a < NP; ++a) {
+    double acc = 0.0;
+#pragma unroll 1
+    for (int b = 0; b < NP; ++b) acc += (double)ops.Minv[a * NP + b] * (double)r[0][b];
+    dV[a] = -acc * jinv;
+  }
+#pragma unroll 1
+  for (int i = 0; i < NP * NP; ++i) Mh[i] = 0.0;
+#pragma unroll 1
+  for (int a = 0; a < NP; ++a)
+#pragma unroll 1
+    for (int j = 0; j < DIM; ++j) rhs[j * NP + a] = -(double)r[1 + j][a] * jinv;
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    double hq = 0.0, hdq = 0.0, uq[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) uq[j] = 0.0;
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) {
+      const double l = (double)ops.Vq[q * NP + a];
+      hq += l * V[a];
+      hdq += l * dV[a];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) uq[j] += l * V[(1 + j) * NP + a];
+    }
+    const double wh = (double)ops.wq[q] * fmax(hq, hf);
+    const double wd = (double)ops.wq[q] * hdq;
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) {
+      const double la = (double)ops.Vq[q * NP + a];
+      const double t = wh * la;
+#pragma unroll 1
+      for (int b = 0; b <= a; ++b) Mh[a * NP + b] += t * (double)ops.Vq[q * NP + b];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) rhs[j * NP + a] -= wd * uq[j] * la;
+    }
+  }
+#pragma unroll 1
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll 1
+    for (int b = 0; b < a; ++b) {
+      double sum = Mh[a * NP + b];
+#pragma unroll 1
+      for (int c = 0; c < b; ++c) sum -= Mh[a * NP + c] * Mh[b * NP + c];
+      Mh[a * NP + b] = sum * dinv[b];
+    }
+    double d = Mh[a * NP + a];
+#pragma unroll 1
+    for (int c = 0; c < a; ++c) d -= Mh[a * NP + c] * Mh[a * NP + c];
+    dinv[a] = rsqrt(d);
+  }
+#pragma unroll 1
+  for (int j = 0; j < DIM; ++j) {
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) {
+      double sum = rhs[j * NP + a];
+#pragma unroll 1
+      for (int c = 0; c < a; ++c) sum -= Mh[a * NP + c] * y[c];
+      y[a] = sum * dinv[a];
+    }
+#pragma unroll 1
+    for (int a = NP - 1; a >= 0; --a) {
+      double sum = y[a];
+#pragma unroll 1
+      for (int c = a + 1; c < NP; ++c) sum -= Mh[c * NP + a] * dV[(1 + j) * NP + c];
+      dV[(1 + j) * NP + a] = sum * dinv[a];
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) dVout[v][a] = (float)dV[v * NP + a];
+}
+
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void mass_solve_dispatch(const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                                    const R (&r)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                                    const VolOps<DIM, P, R>& ops, const Phys<R>& ph, R Jinv,
+                                                    R (&dV)[Sh<DIM, P>::NV][Sh<DIM, P>::NP]) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP;
+  if constexpr (sizeof(R) == 4) {
+    R hmin = Vn[0][0];
+#pragma unroll
+    for (int a = 1; a < NP; ++a) hmin = fmin(hmin, Vn[0][a]);
+    if (hmin < ph.h_dry) {
+      mass_solve_dry<DIM, P>(Vn, r, ops, ph.h_floor, Jinv, dV);
+      return;
+    }
+  }
+  mass_solve_element<DIM, P, R>(Vn, r, ops, ph.h_floor, Jinv, dV);
+}
+
 // Per-volume-point operator rows (Vq, Wr, Ws, Wm, Drq, Dsq) of the direct
 // FP64 2D volume kernel, copied once per block into shared memory with each
 // row padded to 16 bytes, so that a row arrives in 128-bit loads instead of
@@ -887,7 +1009,7 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 
   // ---- mass solve: M dh/dt = -r_h ; M_h du/dt = -r_u - M_u dh/dt
   R dV[NV][NP];
-  mass_solve_element<DIM, P, R>(Vn, r, ops, ph.h_floor, dg_div<R>(R(1), J), dV);
+  mass_solve_dispatch<DIM, P, R>(Vn, r, ops, ph, dg_div<R>(R(1), J), dV);
 
   // ---- output
   if (mode == 0) {

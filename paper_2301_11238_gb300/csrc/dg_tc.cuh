@@ -576,12 +576,28 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int j = 0; j < 2; ++j) rhs[j][a] -= wd * uqs[j][q] * la;
             }
           }
+          // near-dry element (smallest nodal depth below h_dry): the whole
+          // mass solve again in FP64 from the nodal values, as in the
+          // CUDA-core kernel (mass_solve_dispatch)
+          float hmin = Vin[eo];
+#pragma unroll
+          for (int a = 1; a < NP; ++a) hmin = fminf(hmin, Vin[eo + a]);
+          const bool dry = hmin < ph.h_dry;
+          if (dry) {
+            float Vn[NV][NP];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+              for (int a = 0; a < NP; ++a) Vn[v][a] = Vin[v * KN + eo + a];
+            mass_solve_dry<2, P>(Vn, r, ops, ph.h_floor, Jinv, dV);
+          }
           float Mh[NP][NP];
 #pragma unroll
           for (int a = 0; a < NP; ++a)
 #pragma unroll
             for (int b = 0; b <= a; ++b) Mh[a][b] = d3[a * (a + 1) / 2 + b];
           float dinv[NP];
+          if (!dry) {
 #pragma unroll
           for (int a = 0; a < NP; ++a) {
 #pragma unroll
@@ -613,6 +629,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               for (int cc = a + 1; cc < NP; ++cc) s -= Mh[cc][a] * dV[1 + j][cc];
               dV[1 + j][a] = s * dinv[a];
             }
+          }
           }
           if (mode == 0) {
 #pragma unroll

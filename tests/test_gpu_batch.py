@@ -111,15 +111,22 @@ def _run_with_volume_tiles(cases, precision, vol_tile, steps):
 @pytest.mark.parametrize("prec", [0, 1])
 def test_staged_volume_bitwise_equal_to_direct(prec):
     """The staged volume kernel (bulk copies into shared memory, negative
-    block size) does the same arithmetic as the direct one: bitwise equal
-    states after 12 steps, for 1D/2D groups of every order, with and
-    without a bed, through every RK stage (c0 = 0 and c0 != 0)."""
+    block size) does the same arithmetic as the direct one: in FP64 bitwise
+    equal states after 12 steps, for 1D/2D groups of every order, with and
+    without a bed, through every RK stage (c0 = 0 and c0 != 0).  In FP32 the
+    two kernels inline the same element code, but the compiler may fuse its
+    multiply-adds differently in each (seen once the near-dry FP64 mass solve
+    joined that code: 5.7e-11 relative after 12 steps on the p = 3 bump), so
+    FP32 states agree to 1e-9 relative, far below FP32 rounding."""
     cases = _mixed_cases()
     ref = _run_with_volume_tiles(cases, prec, 64, 12)
     for T in (-32, -64, -128):
         got = _run_with_volume_tiles(cases, prec, T, 12)
         for i in range(len(cases)):
-            assert np.array_equal(got[i], ref[i]), (T, i, rel_l2(got[i], ref[i]))
+            if prec == 0:
+                assert np.array_equal(got[i], ref[i]), (T, i, rel_l2(got[i], ref[i]))
+            else:
+                assert rel_l2(got[i], ref[i]) < 1e-9, (T, i, rel_l2(got[i], ref[i]))
 
 
 @pytest.mark.parametrize("prec", [0, 1])
