@@ -461,7 +461,7 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
     g.inst.insert(g.inst.end(), (size_t)K, (int32_t)i);
     g.gid.push_back(i);
     // per-member SoA blocks, interleaved into group SoA arrays below
-    g.geo.insert(g.geo.end(), m.geo.begin(), m.geo.end());            // [6][K] blocks, interleaved later
+    g.geo.insert(g.geo.end(), m.geo.begin(), m.geo.end());            // [kGeoRows][K] blocks, interleaved later
     for (int64_t k = 0; k < nf * K; ++k) g.nbr.push_back(remap_nbr(m.nbr[k]));
     g.nbrf.insert(g.nbrf.end(), m.nbrf.begin(), m.nbrf.end());
     for (int64_t k = 0; k < nf * K; ++k) {
@@ -507,7 +507,7 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
   for (auto& g : b->groups) {
     const int nf = g.dim + 1, dim = g.dim;
     const int64_t Kg = g.K, Fg = g.F;
-    std::vector<double> geo(6 * Kg), fn((size_t)nf * dim * Kg), fsj(nf * Kg), fnm((size_t)dim * Fg);
+    std::vector<double> geo(kGeoRows * Kg), fn((size_t)nf * dim * Kg), fsj(nf * Kg), fnm((size_t)dim * Fg);
     std::vector<int32_t> nbr(nf * Kg), fid(nf * Kg);
     std::vector<int8_t> nbrf(nf * Kg);
     size_t pg = 0, pn = 0, pfn = 0, pfs = 0, pfnm = 0;
@@ -515,9 +515,9 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
       const int64_t eb = g.ebase[mi], fb = g.fbase[mi];
       const int64_t K = (mi + 1 < g.members.size() ? g.ebase[mi + 1] : Kg) - eb;
       const int64_t F = (mi + 1 < g.members.size() ? g.fbase[mi + 1] : Fg) - fb;
-      for (int c = 0; c < 6; ++c)
+      for (int c = 0; c < kGeoRows; ++c)
         for (int64_t e = 0; e < K; ++e) geo[c * Kg + eb + e] = g.geo[pg + c * K + e];
-      pg += 6 * K;
+      pg += kGeoRows * K;
       for (int f = 0; f < nf; ++f)
         for (int64_t e = 0; e < K; ++e) {
           nbr[f * Kg + eb + e] = g.nbr[pn + f * K + e];
@@ -570,7 +570,7 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
   for (auto& g : b->groups) {
     const int64_t K = g.K, F = g.F;
     const int nf = g.dim + 1, Np = g.ops.Np, nV = g.dim + 1, nE = g.dim * g.dim;
-    g.off.geo = take(6 * K * rs);
+    g.off.geo = take(kGeoRows * K * rs);
     g.off.nbr = take(nf * K * 4);
     g.off.nbrf = take(nf * K);
     g.off.fid = take(nf * K * 4);

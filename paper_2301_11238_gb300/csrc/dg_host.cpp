@@ -283,7 +283,7 @@ bool build_mesh(int dim, int64_t nvtx, const double* X, int64_t K, const int32_t
   m.dim = dim;
   m.nf = nf;
   m.K = K;
-  m.geo.assign(6 * K, 0.0);
+  m.geo.assign(kGeoRows * K, 0.0);
   m.nbr.assign(nf * K, 0);
   m.nbrf.assign(nf * K, 0);
   m.fid.assign(nf * K, 0);
@@ -311,6 +311,7 @@ bool build_mesh(int dim, int64_t nvtx, const double* X, int64_t K, const int32_t
       m.geo[0 * K + e] = 1.0 / J;
       m.geo[4 * K + e] = J;
       m.geo[5 * K + e] = 2.0 * J;
+      m.geo[6 * K + e] = 1.0 / J;
       m.fn[(0 * dim + 0) * K + e] = -1.0;
       m.fn[(1 * dim + 0) * K + e] = 1.0;
       m.fsj[0 * K + e] = 1.0;
@@ -346,6 +347,7 @@ bool build_mesh(int dim, int64_t nvtx, const double* X, int64_t K, const int32_t
         m.fsj[f * K + e] = 0.5 * len;
       }
       m.geo[5 * K + e] = 4.0 * (2.0 * J) / perim;  // twice the inradius
+      m.geo[6 * K + e] = 1.0 / J;
       for (int a = 0; a < Np; ++a) {
         double l1 = 0.5 * (1.0 + ops.rnodes[a * 2]), l2 = 0.5 * (1.0 + ops.rnodes[a * 2 + 1]);
         double l0 = 1.0 - l1 - l2;

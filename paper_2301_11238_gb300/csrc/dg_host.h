@@ -20,6 +20,11 @@
 
 namespace dgswe {
 
+// rows of the per-element geometry array: dr_a/dx_i (4), J, dx (step-bound
+// length), 1/J (precomputed so the kernels divide by J nowhere)
+constexpr int kGeoRows = 7;
+
+
 // Element-local index of node k of face f in the equispaced nodal ordering.
 // 1D: nodes 0..p from left to right; face 0 is the left end, face 1 the
 // right.  Triangles: node (i, j), i + j <= p, has index
@@ -70,7 +75,7 @@ bool build_refops(int dim, int p, RefOps& ops, std::string& err);
 struct MeshData {
   int dim = 0, nf = 0;
   int64_t K = 0, F = 0;                     // elements, unique faces
-  std::vector<double> geo;                  // [6][K]: G00 G01 G10 G11 (dr_a/dx_i), J, dx
+  std::vector<double> geo;                  // [kGeoRows][K]: G00 G01 G10 G11 (dr_a/dx_i), J, dx, 1/J
   std::vector<int32_t> nbr;                 // [nf][K] neighbour element, or -1-bc for boundary
   std::vector<int8_t> nbrf;                 // [nf][K] neighbour's local face
   std::vector<int32_t> fid;                 // [nf][K] face id; bit 31 set when not the owner

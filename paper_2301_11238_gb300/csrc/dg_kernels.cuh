@@ -190,11 +190,21 @@ __device__ __forceinline__ void stress(const R* E, const Phys<R>& ph, R sig[DIM]
     R d11 = E[0], d22 = E[3], d12 = R(0.5) * (E[1] + E[2]);
     R tr = d11 + d22;
     R nc2 = d11 * d11 + R(2) * d12 * d12 + d22 * d22 + tr * tr;
-    // s = sqrt(nc2 / 2) and 1 / s from one reciprocal square root
     const R s2 = R(0.5) * nc2;
-    const R s_inv = s2 > R(0) ? dg_rsqrt<R>(s2) : R(0);
-    const R s = s2 * s_inv;
-    R mu = R(2) * viscous_eta<R>(s, ph) + bingham_coef<R>(s, s_inv, ph);
+    R mu;
+    if (ph.reg == 5 && !ph.hb) {
+      // bi-viscosity with the Newtonian viscous part: gamma below the yield
+      // rate (gamma s < sigma0, tested on s^2) and sigma0 / s above it, so
+      // the reciprocal square root is taken only where the material yields
+      const R g = ph.gamma, s0 = ph.sigma0;
+      const R coef = s0 == R(0) ? R(0) : (g * g * s2 < s0 * s0 ? g : s0 * dg_rsqrt<R>(s2));
+      mu = R(2) * ph.eta + coef;
+    } else {
+      // s = sqrt(nc2 / 2) and 1 / s from one reciprocal square root
+      const R s_inv = s2 > R(0) ? dg_rsqrt<R>(s2) : R(0);
+      const R s = s2 * s_inv;
+      mu = R(2) * viscous_eta<R>(s, ph) + bingham_coef<R>(s, s_inv, ph);
+    }
     sig[0][0] = mu * (d11 + tr);
     sig[1][1] = mu * (d22 + tr);
     sig[0][1] = mu * d12;
@@ -316,7 +326,7 @@ __global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__
     G[1][0] = geo[2 * K + e];
     G[1][1] = geo[3 * K + e];
   }
-  const R Jinv = dg_div<R>(R(1), geo[4 * K + e]);
+  const R Jinv = geo[6 * K + e];
   R Eo[NE][NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) {
@@ -1009,7 +1019,7 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 
   // ---- mass solve: M dh/dt = -r_h ; M_h du/dt = -r_u - M_u dh/dt
   R dV[NV][NP];
-  mass_solve_dispatch<DIM, P, R>(Vn, r, ops, ph, dg_div<R>(R(1), J), dV);
+  mass_solve_dispatch<DIM, P, R>(Vn, r, ops, ph, geo[6 * K + e], dV);
 
   // ---- output
   if (mode == 0) {
@@ -1144,7 +1154,7 @@ __global__ void __launch_bounds__(256) mass_precond_kernel(int K, const R* __res
       Vn[v][a] = V[v * KN + eo + a];
       xr[v][a] = x[v * KN + eo + a];
     }
-  mass_solve_element<DIM, P, R>(Vn, xr, ops, h_floor, dg_div<R>(R(1), geo[4 * K + e]), dV);
+  mass_solve_element<DIM, P, R>(Vn, xr, ops, h_floor, geo[6 * K + e], dV);
 #pragma unroll
   for (int v = 0; v < NV; ++v)
 #pragma unroll

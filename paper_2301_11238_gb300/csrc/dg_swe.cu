@@ -345,7 +345,7 @@ dg_status dg_swe_init(const dg_swe_mesh* mesh, int order, int regularization, co
   };
   c->nblk_dt = (int)((K + kRedBlock - 1) / kRedBlock);
   c->nblk_mass = c->nblk_dt;
-  c->off.geo = take(6 * K * rs);
+  c->off.geo = take(kGeoRows * K * rs);
   c->off.nbr = take(nf * K * 4);
   c->off.nbrf = take(nf * K);
   c->off.fid = take(nf * K * 4);

@@ -549,7 +549,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int a = 0; a < NP; ++a) out[v * KN + eo + a] = r[v][a];
         } else {
           // M dh/dt = -r_h ; M_h du/dt = -r_u - M_u dh/dt (Appendix A, dU/dV)
-          const float Jinv = dg_div<float>(1.0f, J);
+          const float Jinv = geo[6 * K + e];
           float dV[NV][NP];
 #pragma unroll
           for (int a = 0; a < NP; ++a) {
