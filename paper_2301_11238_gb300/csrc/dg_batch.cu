@@ -43,12 +43,16 @@ struct Group {
   std::vector<int64_t> ebase, fbase;  // per member
   // host staging (uploaded by set_workspace)
   std::vector<double> geo, fn, fsj, face_n, face_sj, bed;
+  // per member: its bed/slope source coefficients [dim * Nq][K_m] (a flat-bed
+  // member of a group with beds: -g_s and 0); interleaved into src
+  std::vector<std::vector<double>> src_blocks;
+  std::vector<double> src, gs_of;
   std::vector<int32_t> nbr, fid, fe1, fe2, inst, gid;
   std::vector<int8_t> nbrf, ff1, ff2;
   std::vector<int64_t> ebeg;
   struct {
     size_t geo, nbr, nbrf, fid, fn, fsj, fe1, fe2, ff1, ff2, fnrm, fsjf, bed, inst, ebeg, gid, V[3], E, wflux, wint,
-        blk_e, blk_gid, mblk, partial, tcimg;
+        blk_e, blk_gid, mblk, partial, tcimg, src;
   } off{};
   std::vector<int64_t> blk_e;      // step-size blocks: element ranges (n_blk + 1)
   std::vector<int32_t> blk_gid;    // global instance of each block
@@ -239,7 +243,8 @@ struct GDrv final : GroupDrv {
       if (grid <= 0) return;
       volume_staged_kernel<DIM, P, R><<<grid, T, staged_smem_bytes<DIM, P, R>(T), s>>>(
           K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.V[0]), b->at<R>(g.off.V[vout]), b->at<R>(g.off.E),
-          g.has_bed ? b->at<R>(g.off.bed) : nullptr, b->at<R>(g.off.geo), b->at<int32_t>(g.off.fid),
+          g.has_bed ? b->at<R>(g.off.bed) : nullptr, g.has_bed ? b->at<R>(g.off.src) : nullptr,
+          b->at<R>(g.off.geo), b->at<int32_t>(g.off.fid),
           b->at<R>(g.off.wflux), vo, ptab(b), b->at<int32_t>(g.off.inst), (R)c0, (R)c1,
           b->at<DevScalars>(b->off_sc));
       return;
@@ -247,7 +252,8 @@ struct GDrv final : GroupDrv {
     const int T = g.tile[2];
     volume_kernel<DIM, P, R, true><<<(K + T - 1) / T, T, 0, s>>>(
         K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.V[0]), b->at<R>(g.off.V[vout]), b->at<R>(g.off.E),
-        g.has_bed ? b->at<R>(g.off.bed) : nullptr, b->at<R>(g.off.geo), b->at<int32_t>(g.off.fid),
+        g.has_bed ? b->at<R>(g.off.bed) : nullptr, g.has_bed ? b->at<R>(g.off.src) : nullptr,
+          b->at<R>(g.off.geo), b->at<int32_t>(g.off.fid),
         b->at<R>(g.off.wflux), vo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), 1, (R)c0, (R)c1,
         b->at<DevScalars>(b->off_sc));
   }
@@ -488,6 +494,8 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
     } else if (g.has_bed) {
       g.bed.insert(g.bed.end(), (size_t)K * Np, 0.0);
     }
+    g.src_blocks.push_back(c->has_bed ? c->src : std::vector<double>());
+    g.gs_of.push_back(params[i].g * std::sin(params[i].alpha));
     // per-instance tables
     if (b->rsize == 8) push_phys<double>(params[i], regs[i], phys_bytes);
     else push_phys<float>(params[i], regs[i], phys_bytes);
@@ -533,6 +541,20 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
         for (int64_t f = 0; f < F; ++f) fnm[d * Fg + fb + f] = g.face_n[pfnm + d * F + f];
       pfnm += (size_t)dim * F;
     }
+    if (g.has_bed) {  // source coefficients, [dim * Nq][Kg]
+      const int rows = dim * g.ops.Nq;
+      g.src.assign((size_t)rows * Kg, 0.0);
+      for (size_t mi = 0; mi < g.members.size(); ++mi) {
+        const int64_t eb = g.ebase[mi];
+        const int64_t K = (mi + 1 < g.members.size() ? g.ebase[mi + 1] : Kg) - eb;
+        const std::vector<double>& blk = g.src_blocks[mi];
+        for (int r = 0; r < rows; ++r)
+          for (int64_t e = 0; e < K; ++e)
+            g.src[(size_t)r * Kg + eb + e] =
+                blk.empty() ? (r < g.ops.Nq ? -g.gs_of[mi] : 0.0) : blk[(size_t)r * K + e];
+      }
+    }
+    g.src_blocks.clear();
     g.geo.swap(geo);
     g.fn.swap(fn);
     g.fsj.swap(fsj);
@@ -583,6 +605,7 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
     g.off.fnrm = take((size_t)g.dim * F * rs);
     g.off.fsjf = take(F * rs);
     g.off.bed = take(g.has_bed ? K * Np * rs : 0);
+    g.off.src = take(g.has_bed ? g.src.size() * rs : 0);
     g.off.inst = take(K * 4);
     g.off.ebeg = take(g.ebeg.size() * 8);
     g.off.gid = take(g.gid.size() * 4);
@@ -648,6 +671,7 @@ dg_status dg_batch_set_workspace(dg_batch* b, void* ptr, size_t bytes) {
     BK(upr(g.off.fnrm, g.face_n));
     BK(upr(g.off.fsjf, g.face_sj));
     if (g.has_bed) BK(upr(g.off.bed, g.bed));
+    if (g.has_bed) BK(upr(g.off.src, g.src));
     BK(up(g.off.inst, g.inst.data(), g.inst.size() * 4));
     BK(up(g.off.ebeg, g.ebeg.data(), g.ebeg.size() * 8));
     BK(up(g.off.gid, g.gid.data(), g.gid.size() * 4));

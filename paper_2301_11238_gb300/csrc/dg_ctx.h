@@ -45,6 +45,7 @@ struct dg_swe_ctx {
   dgswe::RefOps ops;
   dgswe::MeshData mesh;
   std::vector<double> bed;
+  std::vector<double> src;  // bed/slope source coefficients at the volume points, [dim * Nq][K] (bed only)
   bool has_bed = false;
   size_t rsize = 8;
   int device = -1;  // device current at dg_swe_set_workspace (the workspace's device)
@@ -53,7 +54,7 @@ struct dg_swe_ctx {
   char* ws = nullptr;
   struct {
     size_t geo, nbr, nbrf, fid, fn, fsj, fe1, fe2, ff1, ff2, fnrm, fsjf, bed, V0, V1, V2, E, wflux, partial, wint, sc,
-        bct, tcimg;
+        bct, tcimg, src;
   } off{};
   int nblk_dt = 0, nblk_mass = 0;
   cudaStream_t stream = nullptr;

@@ -440,4 +440,25 @@ bool build_mesh(int dim, int64_t nvtx, const double* X, int64_t K, const int32_t
   return true;
 }
 
+void build_bed_source(int dim, const RefOps& ops, int64_t K, const std::vector<double>& geo,
+                      const std::vector<double>& bed, double gc, double gs, std::vector<double>& src) {
+  const int NQ = ops.Nq, Np = ops.Np;
+  src.assign((size_t)dim * NQ * K, 0.0);
+  for (int64_t e = 0; e < K; ++e)
+    for (int q = 0; q < NQ; ++q) {
+      double Hr = 0.0, Hs = 0.0;
+      for (int a = 0; a < Np; ++a) {
+        Hr += ops.Drq[q * Np + a] * bed[e * Np + a];
+        if (dim == 2) Hs += ops.Dsq[q * Np + a] * bed[e * Np + a];
+      }
+      double dHx = geo[e] * Hr;
+      if (dim == 2) dHx += geo[2 * K + e] * Hs;
+      src[(size_t)q * K + e] = -gc * dHx - gs;
+      if (dim == 2) {
+        const double dHy = geo[K + e] * Hr + geo[3 * K + e] * Hs;
+        src[(size_t)(NQ + q) * K + e] = -gc * dHy;
+      }
+    }
+}
+
 }  // namespace dgswe

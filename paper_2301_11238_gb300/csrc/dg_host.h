@@ -70,6 +70,13 @@ struct RefOps {
 
 bool build_refops(int dim, int p, RefOps& ops, std::string& err);
 
+// Source coefficients of the bed and slope terms of Eq. Sterm at the volume
+// quadrature points: c_j = -g_c dH/dx_j - g_s delta_1j, so that the source of
+// momentum equation j is S_j = h c_j.  The bed H is the element's nodal
+// interpolant; geo is the [kGeoRows][K] geometry.  Layout [dim * Nq][K].
+void build_bed_source(int dim, const RefOps& ops, int64_t K, const std::vector<double>& geo,
+                      const std::vector<double>& bed, double gc, double gs, std::vector<double>& src);
+
 // Geometry and connectivity of a conforming mesh of intervals (dim 1) or
 // counter-clockwise triangles (dim 2).
 struct MeshData {

@@ -377,15 +377,25 @@ __global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__
         for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (Vp[1 + j] - Vm[1 + j]);
       }
     }
+    // the face's jump terms sc n_i [u_j]/2, scaled once per face node
+    R gt[NFP][DIM][DIM];
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) {
+      const R sn = sc * n[i];
+#pragma unroll
+      for (int k = 0; k < NFP; ++k)
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) gt[k][i][j] = sn * gj[k][j];
+    }
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
 #pragma unroll
       for (int k = 0; k < NFP; ++k) {
-        const R L = ops.LIFT[a * (NF * NFP) + f * NFP + k] * sc;
+        const R L = ops.LIFT[a * (NF * NFP) + f * NFP + k];
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
-          for (int j = 0; j < DIM; ++j) Eo[DIM * i + j][a] += L * n[i] * gj[k][j];
+          for (int j = 0; j < DIM; ++j) Eo[DIM * i + j][a] += L * gt[k][i][j];
       }
     }
   }
@@ -776,7 +786,7 @@ __device__ __forceinline__ void mass_solve_dispatch(const R (&Vn)[Sh<DIM, P>::NV
   mass_solve_element<DIM, P, R>(Vn, r, ops, ph.h_floor, Jinv, dV);
 }
 
-// Per-volume-point operator rows (Vq, Wr, Ws, Wm, Drq, Dsq) of the direct
+// Per-volume-point operator rows (Vq, Wr, Ws, Wm) of the direct
 // FP64 2D volume kernel, copied once per block into shared memory with each
 // row padded to 16 bytes, so that a row arrives in 128-bit loads instead of
 // one constant-bank load per value (FP64 headline volume kernel: 0.401 ->
@@ -786,7 +796,7 @@ __device__ __forceinline__ void mass_solve_dispatch(const R (&Vn)[Sh<DIM, P>::NV
 // where the fill cost more than it saved (200-element dam break: -5 %).
 template <int DIM, int P, typename R>
 struct QTab {
-  static constexpr int NP = Sh<DIM, P>::NP, NQ = Sh<DIM, P>::NQ, ROWS = 6;
+  static constexpr int NP = Sh<DIM, P>::NP, NQ = Sh<DIM, P>::NQ, ROWS = 4;
   static constexpr int PAD = (int)(((NP * sizeof(R) + 15) / 16) * 16 / sizeof(R));
   static constexpr bool USED = sizeof(R) == 8 && DIM == 2;
   static constexpr int SIZE = USED ? NQ * ROWS * PAD : 2;
@@ -800,8 +810,7 @@ __device__ __forceinline__ void qtab_fill(R* tab, const VolOps<DIM, P, R>& ops) 
       R v = R(0);
       if (a < T::NP) {
         const int j = q * T::NP + a;
-        v = k == 0 ? ops.Vq[j]
-                   : k == 1 ? ops.Wr[j] : k == 2 ? ops.Ws[j] : k == 3 ? ops.Wm[j] : k == 4 ? ops.Drq[j] : ops.Dsq[j];
+        v = k == 0 ? ops.Vq[j] : k == 1 ? ops.Wr[j] : k == 2 ? ops.Ws[j] : ops.Wm[j];
       }
       tab[i] = v;
     }
@@ -829,15 +838,21 @@ __device__ __forceinline__ void op_row(const VolOps<DIM, P, R>& ops, const R* ta
       return;
     }
   }
-  const R* src = ROW == 0 ? ops.Vq : ROW == 1 ? ops.Wr : ROW == 2 ? ops.Ws : ROW == 3 ? ops.Wm : ROW == 4 ? ops.Drq
-                                                                                                    : ops.Dsq;
+  const R* tabsrc = ROW == 0 ? ops.Vq : ROW == 1 ? ops.Wr : ROW == 2 ? ops.Ws : ops.Wm;
 #pragma unroll
-  for (int a = 0; a < NP; ++a) out[a] = src[q * NP + a];
+  for (int a = 0; a < NP; ++a) out[a] = tabsrc[q * NP + a];
 }
 
 // Everything the volume kernels do for one element e once its nodal values
 // are in registers: volume integrals, face lift, mass solve and output.
-// bed_e: the element's NP bed values (nullptr: flat bed).  V0e[v]: the
+// Bed and slope source S_j = -g_c h dH/dx_j - g_s h delta_1j (Eq. Sterm).
+// FP64 contexts read the coefficients c_j = -g_c dH/dx_j - g_s delta_1j at the
+// volume points from src ([DIM * NQ][K], host-computed once since the bed does
+// not change), which saves the FP64 kernels (bound by the FP64 pipe) the
+// interpolation of the bed gradient; FP32 contexts (latency-bound, where the
+// extra global loads inside the point loop cost more than the arithmetic)
+// interpolate the gradient from the element's nodal bed bed_e.  Both nullptr:
+// flat bed (the slope term -g_s h remains).  V0e[v]: the
 // element's values of field v of the stage's first state (read in mode 1
 // when c0 != 0).  mode 0: write dV/dt to out; mode 1: out = c0 * V0 + c1 * (Vin +
 // dt * dV/dt); mode 2: write the spatial residual r_V of Eq. WeakForm51
@@ -845,7 +860,8 @@ __device__ __forceinline__ void op_row(const VolOps<DIM, P, R>& ops, const R* ta
 template <int DIM, int P, typename R>
 __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
                                                const R (&En)[Sh<DIM, P>::NE][Sh<DIM, P>::NP],
-                                               const R* __restrict__ bed_e, const R* const (&V0e)[Sh<DIM, P>::NV],
+                                               const R* __restrict__ bed_e, const R* __restrict__ src,
+                                               const R* const (&V0e)[Sh<DIM, P>::NV],
                                                R* out,
                                                const R* __restrict__ geo, const int32_t* __restrict__ fid,
                                                const R* __restrict__ wflux, const VolOps<DIM, P, R>& ops,
@@ -869,8 +885,8 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 #pragma unroll
     for (int a = 0; a < NP; ++a) r[v][a] = R(0);
 
-  // the element's bed values, read once
-  const bool has_bed = bed_e != nullptr;
+  const bool has_src = sizeof(R) == 8 && src != nullptr;
+  const bool has_bed = sizeof(R) == 4 && bed_e != nullptr;
   R Hn[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) Hn[a] = has_bed ? bed_e[a] : R(0);
@@ -894,16 +910,6 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
       for (int v = 0; v < NV; ++v) Vq[v] += l * Vn[v][a];
 #pragma unroll
       for (int c = 0; c < NE; ++c) Eq[c] += l * En[c][a];
-    }
-    if (has_bed) {
-      R rdr[NP], rds[NP];
-      op_row<DIM, P, 4>(ops, tab, q, rdr);
-      if constexpr (DIM == 2) op_row<DIM, P, 5>(ops, tab, q, rds);
-#pragma unroll
-      for (int a = 0; a < NP; ++a) {
-        Hr += rdr[a] * Hn[a];
-        if constexpr (DIM == 2) Hs += rds[a] * Hn[a];
-      }
     }
     } else {
 #pragma unroll
@@ -933,7 +939,10 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
     }
     R Sv[NV];
     Sv[0] = R(0);
-    {
+    if (has_src) {
+#pragma unroll
+      for (int jj = 0; jj < DIM; ++jj) Sv[1 + jj] = h * src[(size_t)(jj * NQ + q) * K + e];
+    } else {
       R dH[DIM];
 #pragma unroll
       for (int i = 0; i < DIM; ++i) {
@@ -965,12 +974,14 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
       const R wr = QTab<DIM, P, R>::USED ? rwr[a] : ops.Wr[q * NP + a];
       const R ws = DIM == 1 ? R(0) : QTab<DIM, P, R>::USED ? rws[a] : ops.Ws[q * NP + a];
       const R wm = QTab<DIM, P, R>::USED ? rwm[a] : ops.Wm[q * NP + a];
+      // accumulated straight into r, three fused multiply-adds per entry
 #pragma unroll
       for (int v = 0; v < NV; ++v) {
-        R acc = wr * fr[v];
-        if (v > 0) acc -= wm * Sv[v];  // the depth equation has no source
-        if constexpr (DIM == 2) acc += ws * fs[v];
-        r[v][a] += acc;
+        R t = r[v][a];
+        t += wr * fr[v];
+        if constexpr (DIM == 2) t += ws * fs[v];
+        if (v > 0) t -= wm * Sv[v];  // the depth equation has no source
+        r[v][a] = t;
       }
     }
   }
@@ -998,12 +1009,9 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
     for (int k = 0; k < NFP; ++k) {
       const int a = face_node(DIM, P, f, k);
 #pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        R acc = R(0);
+      for (int v = 0; v < NV; ++v)
 #pragma unroll
-        for (int m = 0; m < NFQ; ++m) acc += ops.LfT[k * NFQ + m] * fv[v][m];
-        r[v][a] += acc;
-      }
+        for (int m = 0; m < NFQ; ++m) r[v][a] += ops.LfT[k * NFQ + m] * fv[v][m];
     }
   }
 
@@ -1050,7 +1058,7 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 template <int DIM, int P, typename R, bool BATCH>
 __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __restrict__ Vin,
                                                      const R* V0, R* out,
-                                                     const R* __restrict__ E, const R* __restrict__ bed,
+                                                     const R* __restrict__ E, const R* __restrict__ bed, const R* __restrict__ src,
                                                      const R* __restrict__ geo, const int32_t* __restrict__ fid,
                                                      const R* __restrict__ wflux, const VolOps<DIM, P, R> ops,
                                                      const Phys<R> ph0, const Phys<R>* __restrict__ ptab,
@@ -1079,7 +1087,7 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
   const R* V0e[NV];
 #pragma unroll
   for (int v = 0; v < NV; ++v) V0e[v] = V0 ? V0 + v * KN + eo : nullptr;
-  volume_element<DIM, P, R>(e, K, F, Vn, En, bed ? bed + eo : nullptr, V0e, out, geo, fid, wflux, ops, ph, ins, mode,
+  volume_element<DIM, P, R>(e, K, F, Vn, En, bed ? bed + eo : nullptr, src, V0e, out, geo, fid, wflux, ops, ph, ins, mode,
                             c0, c1, sc, tab);
 }
 
@@ -1215,7 +1223,7 @@ template <typename R>
 __host__ __device__ constexpr uint32_t staged_slot_bytes(int T, int NP) {
   return (uint32_t)(((size_t)T * NP * sizeof(R) + 16 + 15) & ~size_t(15));
 }
-// Staged arrays per buffer: V (NV fields), E (NE), bed, V0 (NV).
+// Staged arrays per buffer: V (NV fields), E (NE), bed (FP32 only), V0 (NV).
 template <int DIM, int P>
 __host__ __device__ constexpr int staged_arrays() {
   return 2 * Sh<DIM, P>::NV + Sh<DIM, P>::NE + 1;
@@ -1228,7 +1236,7 @@ __host__ __device__ constexpr size_t staged_smem_bytes(int T) {
 // Staged form of volume_kernel for batch groups (same arithmetic, bitwise
 // equal results).  A persistent grid walks tiles of T = blockDim.x
 // consecutive elements.  While a tile is computed, the element-major nodal
-// arrays of the CTA's next tile -- V, E, the bed and (stages with c0 != 0)
+// arrays of the CTA's next tile -- V, E, the bed (FP32) and (stages with c0 != 0)
 // V0, each a contiguous range per field -- arrive in the other of two
 // shared-memory buffers by bulk asynchronous copies, one thread issuing them
 // and an mbarrier per buffer counting the bytes.  Each copy covers the
@@ -1240,7 +1248,7 @@ __host__ __device__ constexpr size_t staged_smem_bytes(int T) {
 template <int DIM, int P, typename R>
 __global__ void __launch_bounds__(256) volume_staged_kernel(int K, int F, const R* __restrict__ Vin, const R* V0,
                                                             R* out, const R* __restrict__ E,
-                                                            const R* __restrict__ bed, const R* __restrict__ geo,
+                                                            const R* __restrict__ bed, const R* __restrict__ src, const R* __restrict__ geo,
                                                             const int32_t* __restrict__ fid,
                                                             const R* __restrict__ wflux, const VolOps<DIM, P, R> ops,
                                                             const Phys<R>* __restrict__ ptab,
@@ -1261,7 +1269,7 @@ __global__ void __launch_bounds__(256) volume_staged_kernel(int K, int F, const 
     const R* base;
     if (j < NV) base = Vin + j * KN;
     else if (j < NV + NE) base = E + (j - NV) * KN;
-    else if (j == NV + NE) base = bed;
+    else if (j == NV + NE) base = sizeof(R) == 4 ? bed : nullptr;  // FP64 reads the source coefficients instead
     else base = need_v0 ? V0 + (j - NV - NE - 1) * KN : nullptr;
     return base ? reinterpret_cast<const char*>(base + (size_t)e0 * NP) : nullptr;
   };
@@ -1342,7 +1350,7 @@ __global__ void __launch_bounds__(256) volume_staged_kernel(int K, int F, const 
       const R* V0e[NV];
 #pragma unroll
       for (int v = 0; v < NV; ++v) V0e[v] = sV[NV + NE + 1 + v];
-      volume_element<DIM, P, R>(e, K, F, Vn, En, bed ? sV[NV + NE] : nullptr, V0e, out, geo, fid, wflux, ops, ph,
+      volume_element<DIM, P, R>(e, K, F, Vn, En, (sizeof(R) == 4 && bed) ? sV[NV + NE] : nullptr, src, V0e, out, geo, fid, wflux, ops, ph,
                                 ins, 1, c0, c1, sc, nullptr);
     }
     __syncthreads();

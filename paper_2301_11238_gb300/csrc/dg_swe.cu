@@ -134,7 +134,8 @@ struct Impl final : Driver {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     volume_kernel<DIM, P, R, false><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
         K, F, (const R*)Vin, (const R*)V0, (R*)out, c->at<R>(c->off.E),
-        c->has_bed ? c->at<R>(c->off.bed) : nullptr, c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid),
+        c->has_bed ? c->at<R>(c->off.bed) : nullptr, c->has_bed ? c->at<R>(c->off.src) : nullptr,
+        c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid),
         c->at<R>(c->off.wflux), vo, ph, nullptr, nullptr, mode, (R)c0, (R)c1, c->at<DevScalars>(c->off.sc));
   }
   void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) override {
@@ -162,6 +163,7 @@ struct Impl final : Driver {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     volume_kernel<DIM, P, R, false><<<(K + kBlock - 1) / kBlock, kBlock, 0, s>>>(
         K, F, (const R*)V, nullptr, (R*)out, (const R*)E, c->has_bed ? c->at<R>(c->off.bed) : nullptr,
+        c->has_bed ? c->at<R>(c->off.src) : nullptr,
         c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid), (const R*)wflux, vo, ph, nullptr, nullptr, 0, R(0), R(0),
         c->at<DevScalars>(c->off.sc));
   }
@@ -333,6 +335,8 @@ dg_status dg_swe_init(const dg_swe_mesh* mesh, int order, int regularization, co
   if (mesh->bed) {
     c->has_bed = true;
     c->bed.assign(mesh->bed, mesh->bed + K * Np);
+    build_bed_source(c->dim, c->ops, K, c->mesh.geo, c->bed, p.g * std::cos(p.alpha), p.g * std::sin(p.alpha),
+                     c->src);
   }
   c->drv = c->prec == DG_PREC_FP64 ? make_driver<double>(*c) : make_driver<float>(*c);
   // workspace layout
@@ -358,6 +362,7 @@ dg_status dg_swe_init(const dg_swe_mesh* mesh, int order, int regularization, co
   c->off.fnrm = take((size_t)c->dim * F * rs);
   c->off.fsjf = take(F * rs);
   c->off.bed = take(c->has_bed ? K * Np * rs : 0);
+  c->off.src = take(c->has_bed ? (size_t)c->dim * c->ops.Nq * K * rs : 0);
   c->off.V0 = take((size_t)nV * K * Np * rs);
   c->off.V1 = take((size_t)nV * K * Np * rs);
   c->off.V2 = take((size_t)nV * K * Np * rs);
@@ -417,6 +422,7 @@ dg_status dg_swe_set_workspace(dg_swe_ctx* c, void* ptr, size_t bytes) {
   CK(up_real(c->off.fnrm, m.face_n));
   CK(up_real(c->off.fsjf, m.face_sj));
   if (c->has_bed) CK(up_real(c->off.bed, c->bed));
+  if (c->has_bed) CK(up_real(c->off.src, c->src));
   CK(cudaMemcpyAsync(c->ws + c->off.wint, c->ops.wint.data(), c->ops.Np * 8, cudaMemcpyHostToDevice, s));
   if (c->rsize == 8) {
     auto t = make_bc_table<double>(c->prm);
