@@ -63,6 +63,8 @@ def parse():
                     help="squares per side of the 2D mesh (radial 64, bump 512, slump 2048); "
                          "smaller values give profiling cases of the same kernels")
     ap.add_argument("--order", type=int, default=2)
+    ap.add_argument("--persistent", action="store_true",
+                    help="batch mode: one persistent launch per group and step (dg_batch_set_persistent)")
     ap.add_argument("--tiles", default=None,
                     help="JSON list of [estep, face, volume] block sizes per group (encoded as in "
                          "dg_batch_set_tiles) instead of the autotuner's choice; for profiling")
@@ -598,6 +600,8 @@ def measure(args, G, cases, prec, stream, flush, world, local, clocks=True, e2e_
                 tiles = batch.tiles()
             else:
                 tiles = batch.autotune(5)
+            if args.persistent:
+                batch.set_persistent(True)
             units_per_inner = batch.info()["dofs"]
             launches_per_step = batch.launches_per_step() * args.inner
         else:
@@ -858,6 +862,8 @@ def main():
                        "elements_total": int(sum(c.etov.shape[0] for c in cases)), "mode": args.mode,
                        "tiles": r["tiles"],
                        "inner_rk3_steps_per_step": args.inner, "l2": "flushed (256 MiB write) before each step",
+                       "launch": "persistent (one launch per group and step)" if args.persistent else
+                                 "graph of 11 launches per group and step",
                        "parallelism": f"replicas x{world}", "dt_last": dt_info,
                        "simulated_time_per_step": {k: v * args.inner for k, v in dt_info.items()},
                        "sms": sms},

@@ -91,6 +91,23 @@ dg_status dg_batch_time_kernels(dg_batch *b, int n_iter, double *ms, int cap);
 /* Totals: elements, DOF (elements x nodes x V fields) and groups. */
 dg_status dg_batch_info(const dg_batch *b, int64_t *elements, int64_t *dofs, int32_t *n_groups);
 int32_t dg_batch_launches_per_step(const dg_batch *b);
+
+/* Selects how a step is enqueued (the default, on = 0: for every (dimension,
+ * order) group, the step-size reduction, then for each of the three SSP-RK3
+ * stages the E-step, face-flux and volume kernels: 11 launches per group,
+ * replayed from a CUDA graph).  on != 0: one persistent launch per group and
+ * step, whose thread blocks claim the same work (128-element and
+ * 128-face-point tiles, per-instance step sizes) in a fixed order from a
+ * global counter and wait, per instance, only for the phase before theirs,
+ * so the phases of different instances overlap; the arithmetic is the same
+ * (FP64 results agree to rounding: the compiler may fuse some multiply-adds
+ * differently in the two kernels).  Waits are bounded (one second); a wait that
+ * gives up latches DG_ERR_TIMEOUT for its instance (reported by the next
+ * synchronizing call).  Discards captured graphs.  Returns
+ * DG_ERR_UNSUPPORTED for DG_PREC_FP32_TC batches (the persistent step runs
+ * the CUDA-core volume pass).  (A launch structure of
+ * this library's explicit integrator; the paper's scheme is implicit.) */
+dg_status dg_batch_set_persistent(dg_batch *b, int on);
 const char *dg_batch_last_error(const dg_batch *b);
 void dg_batch_destroy(dg_batch *b);
 

@@ -396,6 +396,11 @@ class Batch:
         self._check(self.L.dg_batch_info(self.ctx, C.byref(K), C.byref(D), C.byref(G_)))
         return dict(elements=K.value, dofs=D.value, groups=G_.value)
 
+    def set_persistent(self, on=True):
+        """One persistent launch per group and step instead of 11 launches
+        (include/dg_batch.h: dg_batch_set_persistent)."""
+        self._check(self.L.dg_batch_set_persistent(self.ctx, 1 if on else 0))
+
     def launches_per_step(self):
         return int(self.L.dg_batch_launches_per_step(self.ctx))
 

@@ -119,6 +119,7 @@ _OPTIONAL_SIGS = {
     "dg_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]),
     "dg_batch_last_error": (C.c_char_p, [C.c_void_p]),
     "dg_batch_destroy": (None, [C.c_void_p]),
+    "dg_batch_set_persistent": (C.c_int, [C.c_void_p, C.c_int]),
     "dg_probe_fma_rate": (C.c_int, [C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.POINTER(C.c_double)]),
     "dg_probe_scratch_bytes": (C.c_size_t, []),
 }

@@ -13,6 +13,7 @@
 #include "dg_ctx.h"
 #include "dg_kernels.cuh"
 #include "dg_tc.cuh"
+#include "dg_persist.cuh"
 
 using namespace dgswe;
 
@@ -32,6 +33,8 @@ struct GroupDrv {
   virtual bool volume_ok(int tile) = 0;
   virtual void dt(dg_batch* b, Group& g, cudaStream_t s) = 0;
   virtual void mass(dg_batch* b, Group& g, int first, int count, int set_ref, cudaStream_t s) = 0;
+  // one whole SSP-RK3 step of the group in one persistent launch (dg_persist.cuh)
+  virtual void persistent_step(dg_batch* b, Group& g, cudaStream_t s) = 0;
 };
 
 struct Group {
@@ -52,11 +55,16 @@ struct Group {
   std::vector<int64_t> ebeg;
   struct {
     size_t geo, nbr, nbrf, fid, fn, fsj, fe1, fe2, ff1, ff2, fnrm, fsjf, bed, inst, ebeg, gid, V[3], E, wflux, wint,
-        blk_e, blk_gid, mblk, partial, tcimg, src;
+        blk_e, blk_gid, mblk, partial, tcimg, src, p_etile, p_ftile, p_fbeg, p_tdt, p_cnt;
   } off{};
   std::vector<int64_t> blk_e;      // step-size blocks: element ranges (n_blk + 1)
   std::vector<int32_t> blk_gid;    // global instance of each block
   std::vector<int32_t> mblk;       // first block of each member (members + 1)
+  // plan of the persistent step (dg_persist.cuh): prefixes of element and
+  // face-point tiles per member, first face per member, item range per phase
+  std::vector<int32_t> p_etile, p_ftile;
+  std::vector<int64_t> p_fbeg;
+  int p_pstart[persist::kPhases + 1] = {};
   int tile[3] = {128, 128, 128};
   std::unique_ptr<GroupDrv> drv;
 };
@@ -66,6 +74,7 @@ struct Group {
 struct dg_batch {
   int n = 0, prec = 0;
   size_t rsize = 8;
+  bool persistent = false;  // one persistent launch per group and step (dg_batch_set_persistent)
   std::vector<int> dim, order, reg, group_of, local_of;
   std::vector<int64_t> K_of, Np_of;
   std::vector<dg_swe_params> prm;
@@ -161,6 +170,8 @@ struct GDrv final : GroupDrv {
   size_t smem_optin = 0;     // shared memory a block may use (static + dynamic)
   size_t staged_static = 0;  // the staged kernel's static shared memory
   std::map<int, int> staged_grid;  // staged volume block size -> persistent grid size (0: not launchable)
+  int persist_grid = 0;            // resident blocks of the persistent step kernel (0: not yet queried)
+  void persistent_step(dg_batch* b, Group& g, cudaStream_t s) override;
   explicit GDrv(const RefOps& o, bool use_tc) {
     fill_ops<DIM, P, R>(o, eo, fo, vo);
     if constexpr (kTcForm) {
@@ -280,6 +291,60 @@ struct GDrv final : GroupDrv {
   }
 };
 
+template <int DIM, int P, typename R>
+void GDrv<DIM, P, R>::persistent_step(dg_batch* b, Group& g, cudaStream_t s) {
+  const int nm = (int)g.members.size();
+  persist::Plan pl{};
+  pl.n_members = nm;
+  for (int ph = 0; ph <= persist::kPhases; ++ph) pl.pstart[ph] = g.p_pstart[ph];
+  pl.etile_pre = b->at<int32_t>(g.off.p_etile);
+  pl.ftile_pre = b->at<int32_t>(g.off.p_ftile);
+  pl.ebeg = b->at<int64_t>(g.off.ebeg);
+  pl.fbeg = b->at<int64_t>(g.off.p_fbeg);
+  pl.gid = b->at<int32_t>(g.off.gid);
+  pl.tile_dt = b->at<double>(g.off.p_tdt);
+  pl.done = b->at<int>(g.off.p_cnt);
+  pl.next = pl.done + nm * persist::kPhases;
+  persist::Arrays<R> A{};
+  for (int v = 0; v < 3; ++v) A.V[v] = b->at<R>(g.off.V[v]);
+  A.E = b->at<R>(g.off.E);
+  A.wflux = b->at<R>(g.off.wflux);
+  A.bed = g.has_bed ? b->at<R>(g.off.bed) : nullptr;
+  A.src = g.has_bed ? b->at<R>(g.off.src) : nullptr;
+  A.geo = b->at<R>(g.off.geo);
+  A.fn = b->at<R>(g.off.fn);
+  A.fsj = b->at<R>(g.off.fsj);
+  A.fnrm = b->at<R>(g.off.fnrm);
+  A.fsjf = b->at<R>(g.off.fsjf);
+  A.nbr = b->at<int32_t>(g.off.nbr);
+  A.fid = b->at<int32_t>(g.off.fid);
+  A.fe1 = b->at<int32_t>(g.off.fe1);
+  A.fe2 = b->at<int32_t>(g.off.fe2);
+  A.inst = b->at<int32_t>(g.off.inst);
+  A.nbrf = b->at<int8_t>(g.off.nbrf);
+  A.ff1 = b->at<int8_t>(g.off.ff1);
+  A.ff2 = b->at<int8_t>(g.off.ff2);
+  A.ptab = ptab(b);
+  A.bct = bct(b);
+  A.iparm = b->at<double>(b->off_iparm);
+  A.sc = b->at<DevScalars>(b->off_sc);
+  A.K = (int)g.K;
+  A.F = (int)g.F;
+  if (persist_grid == 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, persist::step_kernel<DIM, P, R>, persist::kThreads, 0) !=
+            cudaSuccess ||
+        nb < 1)
+      nb = 1;
+    cudaGetLastError();
+    persist_grid = nb * (n_sm > 0 ? n_sm : 1);
+  }
+  const int total = g.p_pstart[persist::kPhases];
+  const int grid = std::max(1, std::min(total, persist_grid));
+  cudaMemsetAsync(pl.done, 0, (size_t)(nm * persist::kPhases + 1) * sizeof(int), s);
+  persist::step_kernel<DIM, P, R><<<grid, persist::kThreads, 0, s>>>(pl, A, eo, fo, vo);
+}
+
 template <typename R>
 std::unique_ptr<GroupDrv> make_gdrv(int dim, int p, const RefOps& o, bool use_tc) {
 #define GCASE(D, PP) \
@@ -290,6 +355,10 @@ std::unique_ptr<GroupDrv> make_gdrv(int dim, int p, const RefOps& o, bool use_tc
 }
 
 void enqueue_step(dg_batch* b, cudaStream_t s) {
+  if (b->persistent) {
+    for (auto& g : b->groups) g.drv->persistent_step(b, g, s);
+    return;
+  }
   for (auto& g : b->groups) g.drv->dt(b, g, s);
   const int vin[3] = {0, 1, 2}, vout[3] = {1, 2, 0};
   const double c0[3] = {0.0, 0.75, 1.0 / 3.0}, c1[3] = {1.0, 0.25, 2.0 / 3.0};
@@ -564,6 +633,28 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
     g.fid.swap(fid);
     g.ebeg = g.ebase;
     g.ebeg.push_back(Kg);
+    {  // persistent-step plan
+      const int nfq = g.ops.Nfq, T = persist::kThreads;
+      const size_t nm = g.members.size();
+      g.p_etile.assign(nm + 1, 0);
+      g.p_ftile.assign(nm + 1, 0);
+      g.p_fbeg.assign(nm + 1, 0);
+      for (size_t mi = 0; mi < nm; ++mi) {
+        const int64_t Km = g.ebeg[mi + 1] - g.ebeg[mi];
+        const int64_t Fm = (mi + 1 < nm ? g.fbase[mi + 1] : Fg) - g.fbase[mi];
+        g.p_etile[mi + 1] = g.p_etile[mi] + (int32_t)((Km + T - 1) / T);
+        g.p_ftile[mi + 1] = g.p_ftile[mi] + (int32_t)((Fm * nfq + T - 1) / T);
+        g.p_fbeg[mi] = g.fbase[mi];
+      }
+      g.p_fbeg[nm] = Fg;
+      const int ne = g.p_etile[nm], nfp = g.p_ftile[nm];
+      int acc = 0;
+      for (int ph = 0; ph < persist::kPhases; ++ph) {
+        g.p_pstart[ph] = acc;
+        acc += ph == 1 ? (int)nm : persist::face_phase(ph) ? nfp : ne;
+      }
+      g.p_pstart[persist::kPhases] = acc;
+    }
     g.blk_e.clear();
     g.blk_gid.clear();
     g.mblk.clear();
@@ -617,6 +708,11 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
     g.off.blk_gid = take(g.blk_gid.size() * 4);
     g.off.mblk = take(g.mblk.size() * 4);
     g.off.partial = take(g.blk_gid.size() * 8);
+    g.off.p_etile = take(g.p_etile.size() * 4);
+    g.off.p_ftile = take(g.p_ftile.size() * 4);
+    g.off.p_fbeg = take(g.p_fbeg.size() * 8);
+    g.off.p_tdt = take((size_t)g.p_etile.back() * 8);
+    g.off.p_cnt = take((g.members.size() * persist::kPhases + 1) * 4);
     g.off.tcimg = take(b->prec == DG_PREC_FP32_TC ? tc::image_bytes(g.dim, g.p) : 0);
   }
   b->off_ptab = take(phys_bytes.size());
@@ -679,6 +775,9 @@ dg_status dg_batch_set_workspace(dg_batch* b, void* ptr, size_t bytes) {
     BK(up(g.off.blk_e, g.blk_e.data(), g.blk_e.size() * 8));
     BK(up(g.off.blk_gid, g.blk_gid.data(), g.blk_gid.size() * 4));
     BK(up(g.off.mblk, g.mblk.data(), g.mblk.size() * 4));
+    BK(up(g.off.p_etile, g.p_etile.data(), g.p_etile.size() * 4));
+    BK(up(g.off.p_ftile, g.p_ftile.data(), g.p_ftile.size() * 4));
+    BK(up(g.off.p_fbeg, g.p_fbeg.data(), g.p_fbeg.size() * 8));
     if (b->prec == DG_PREC_FP32_TC && tc::image_bytes(g.dim, g.p) > 0) {
       std::vector<float> img;
       tc::build_image(g.dim, g.p, g.ops, img);
@@ -926,7 +1025,18 @@ dg_status dg_batch_info(const dg_batch* b, int64_t* elements, int64_t* dofs, int
   return DG_OK;
 }
 
-int32_t dg_batch_launches_per_step(const dg_batch* b) { return b ? (int32_t)(11 * b->groups.size()) : 0; }
+int32_t dg_batch_launches_per_step(const dg_batch* b) {
+  return b ? (int32_t)((b->persistent ? 1 : 11) * b->groups.size()) : 0;
+}
+
+dg_status dg_batch_set_persistent(dg_batch* b, int on) {
+  if (!b) return DG_ERR_ARG;
+  if (on && b->prec == DG_PREC_FP32_TC)
+    return bfail(b, DG_ERR_UNSUPPORTED, "the persistent step runs the CUDA-core volume pass; use DG_PREC_FP32");
+  b->persistent = on != 0;
+  destroy_graphs(b);
+  return DG_OK;
+}
 
 const char* dg_batch_last_error(const dg_batch* b) { return b ? b->err.c_str() : "null batch"; }
 

@@ -125,6 +125,15 @@ __device__ __forceinline__ float dg_sqrt<float>(float x) {
   return r;
 }
 
+// Loads of data that another thread block writes during the same launch (the
+// persistent batch kernel, COH = true) go through L2 (ld.global.cg), which is
+// coherent on the GPU; every other kernel (COH = false) loads normally.
+template <bool COH, typename T>
+__device__ __forceinline__ T ldc(const T* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return *p;
+}
+
 // ------------------------------------------------------------------ physics
 
 // phi_k(s) / (2 s) for s >= 0 (limit phi_k'(0)/2 at s = 0): the Bingham
@@ -303,22 +312,21 @@ __device__ __forceinline__ void q_normal(R h, const R* E, const R* n, const Phys
 
 // ------------------------------------------------------------------ kernels
 
-template <int DIM, int P, typename R>
-__global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__ V, R* __restrict__ E,
-                                                    const R* __restrict__ geo, const int32_t* __restrict__ nbr,
-                                                    const int8_t* __restrict__ nbrf, const R* __restrict__ fn,
-                                                    const R* __restrict__ fsj, const EstepOps<DIM, P, R> ops,
-                                                    const BCEntry<R>* __restrict__ bct) {
+// E-step of element e (the body of estep_kernel).
+template <int DIM, int P, typename R, bool COH = false>
+__device__ __forceinline__ void estep_element(int e, int K, const R* __restrict__ V, R* __restrict__ E,
+                                              const R* __restrict__ geo, const int32_t* __restrict__ nbr,
+                                              const int8_t* __restrict__ nbrf, const R* __restrict__ fn,
+                                              const R* __restrict__ fsj, const EstepOps<DIM, P, R>& ops,
+                                              const BCEntry<R>* __restrict__ bct) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NF = S::NF, NFP = S::NFP, NE = S::NE;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= K) return;
   const size_t KN = (size_t)K * NP;
   R u[DIM][NP];
 #pragma unroll
   for (int j = 0; j < DIM; ++j)
 #pragma unroll
-    for (int a = 0; a < NP; ++a) u[j][a] = V[(1 + j) * KN + (size_t)e * NP + a];
+    for (int a = 0; a < NP; ++a) u[j][a] = ldc<COH>(V + (1 + j) * KN + (size_t)e * NP + a);
   R G[2][2];
   G[0][0] = geo[e];
   if constexpr (DIM == 2) {
@@ -361,7 +369,7 @@ __global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__
         const int a = face_node(DIM, P, f, k);
         const int b = ops.fmask[f2 * NFP + (NFP - 1 - k)];
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (V[(1 + j) * KN + (size_t)e2 * NP + b] - u[j][a]);
+        for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (ldc<COH>(V + (1 + j) * KN + (size_t)e2 * NP + b) - u[j][a]);
       }
     } else {
       const BCEntry<R> bc = bct[-1 - e2];
@@ -403,6 +411,17 @@ __global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__
   for (int c = 0; c < NE; ++c)
 #pragma unroll
     for (int a = 0; a < NP; ++a) E[c * KN + (size_t)e * NP + a] = Eo[c][a];
+}
+
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(256) estep_kernel(int K, const R* __restrict__ V, R* __restrict__ E,
+                                                    const R* __restrict__ geo, const int32_t* __restrict__ nbr,
+                                                    const int8_t* __restrict__ nbrf, const R* __restrict__ fn,
+                                                    const R* __restrict__ fsj, const EstepOps<DIM, P, R> ops,
+                                                    const BCEntry<R>* __restrict__ bct) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  estep_element<DIM, P, R>(e, K, V, E, geo, nbr, nbrf, fn, fsj, ops, bct);
 }
 
 // Numerical flux at one face point m from the traces of both sides at the
@@ -465,21 +484,19 @@ constexpr int face_min_blocks() {
 // PERFACE = false: one thread per face point (re-reads the face-node traces
 // for every point); PERFACE = true: one thread per face, traces read once
 // and all edge points evaluated in turn.  Same arithmetic per point.
-template <int DIM, int P, typename R, bool BATCH, bool PERFACE>
-__global__ void __launch_bounds__(256, face_min_blocks<DIM, P, R>())
-    face_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E,
-                                                   const int32_t* __restrict__ fe1, const int8_t* __restrict__ ff1,
-                                                   const int32_t* __restrict__ fe2, const int8_t* __restrict__ ff2,
-                                                   const R* __restrict__ fnrm, const R* __restrict__ fsj,
-                                                   R* __restrict__ wflux, const FaceOps<DIM, P, R> ops,
-                                                   const Phys<R> ph0, const Phys<R>* __restrict__ ptab,
-                                                   const int32_t* __restrict__ inst,
-                                                   const BCEntry<R>* __restrict__ bct) {
+// Flux work of one face-kernel thread tid (one face point, or one face when
+// PERFACE): the body of face_kernel.
+template <int DIM, int P, typename R, bool BATCH, bool PERFACE, bool COH = false>
+__device__ __forceinline__ void face_item(long long tid, int K, int F, const R* __restrict__ V,
+                                          const R* __restrict__ E, const int32_t* __restrict__ fe1,
+                                          const int8_t* __restrict__ ff1, const int32_t* __restrict__ fe2,
+                                          const int8_t* __restrict__ ff2, const R* __restrict__ fnrm,
+                                          const R* __restrict__ fsj, R* __restrict__ wflux,
+                                          const FaceOps<DIM, P, R>& ops, const Phys<R>& ph0,
+                                          const Phys<R>* __restrict__ ptab, const int32_t* __restrict__ inst,
+                                          const BCEntry<R>* __restrict__ bct) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV, NE = S::NE;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long nthreads = PERFACE ? (long long)F : (long long)F * NFQ;
-  if (tid >= nthreads) return;
   const int fc = PERFACE ? (int)tid : (int)(tid / NFQ);
   const int m0 = PERFACE ? 0 : (int)(tid - (long long)fc * NFQ);
   const size_t KN = (size_t)K * NP;
@@ -493,9 +510,9 @@ __global__ void __launch_bounds__(256, face_min_blocks<DIM, P, R>())
   for (int k = 0; k < NFP; ++k) {
     const size_t a = (size_t)e1 * NP + ops.fmask[f1 * NFP + k];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Tm[v][k] = V[v * KN + a];
+    for (int v = 0; v < NV; ++v) Tm[v][k] = ldc<COH>(V + v * KN + a);
 #pragma unroll
-    for (int c = 0; c < NE; ++c) Tm[NV + c][k] = E[c * KN + a];
+    for (int c = 0; c < NE; ++c) Tm[NV + c][k] = ldc<COH>(E + c * KN + a);
   }
   const bool interior = e2 >= 0;
   if (interior) {
@@ -504,9 +521,9 @@ __global__ void __launch_bounds__(256, face_min_blocks<DIM, P, R>())
     for (int k = 0; k < NFP; ++k) {
       const size_t b = (size_t)e2 * NP + ops.fmask[f2 * NFP + (NFP - 1 - k)];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Tp[v][k] = V[v * KN + b];
+      for (int v = 0; v < NV; ++v) Tp[v][k] = ldc<COH>(V + v * KN + b);
 #pragma unroll
-      for (int c = 0; c < NE; ++c) Tp[NV + c][k] = E[c * KN + b];
+      for (int c = 0; c < NE; ++c) Tp[NV + c][k] = ldc<COH>(E + c * KN + b);
     }
   } else {
 #pragma unroll
@@ -524,6 +541,24 @@ __global__ void __launch_bounds__(256, face_min_blocks<DIM, P, R>())
   } else {
     face_point<DIM, P, R>(m0, Tm, Tp, interior, bct, -1 - e2, n, wsj, ops, ph, wflux, FQ, (size_t)tid);
   }
+}
+
+template <int DIM, int P, typename R, bool BATCH, bool PERFACE>
+__global__ void __launch_bounds__(256, face_min_blocks<DIM, P, R>())
+    face_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E,
+                                                   const int32_t* __restrict__ fe1, const int8_t* __restrict__ ff1,
+                                                   const int32_t* __restrict__ fe2, const int8_t* __restrict__ ff2,
+                                                   const R* __restrict__ fnrm, const R* __restrict__ fsj,
+                                                   R* __restrict__ wflux, const FaceOps<DIM, P, R> ops,
+                                                   const Phys<R> ph0, const Phys<R>* __restrict__ ptab,
+                                                   const int32_t* __restrict__ inst,
+                                                   const BCEntry<R>* __restrict__ bct) {
+  constexpr int NFQ = Sh<DIM, P>::NFQ;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nthreads = PERFACE ? (long long)F : (long long)F * NFQ;
+  if (tid >= nthreads) return;
+  face_item<DIM, P, R, BATCH, PERFACE>(tid, K, F, V, E, fe1, ff1, fe2, ff2, fnrm, fsj, wflux, ops, ph0, ptab, inst,
+                                       bct);
 }
 
 // Depth limiter of one element's new stage values y (nodal), applied when
@@ -857,7 +892,7 @@ __device__ __forceinline__ void op_row(const VolOps<DIM, P, R>& ops, const R* ta
 // when c0 != 0).  mode 0: write dV/dt to out; mode 1: out = c0 * V0 + c1 * (Vin +
 // dt * dV/dt); mode 2: write the spatial residual r_V of Eq. WeakForm51
 // (before the mass solve).
-template <int DIM, int P, typename R>
+template <int DIM, int P, typename R, bool COH = false>
 __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
                                                const R (&En)[Sh<DIM, P>::NE][Sh<DIM, P>::NP],
                                                const R* __restrict__ bed_e, const R* __restrict__ src,
@@ -1002,7 +1037,7 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int m = 0; m < NFQ; ++m) {
-        const R x = wflux[v * FQ + base + (own ? m : NFQ - 1 - m)];
+        const R x = ldc<COH>(wflux + v * FQ + base + (own ? m : NFQ - 1 - m));
         fv[v][m] = own ? x : -x;
       }
 #pragma unroll
@@ -1036,14 +1071,14 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 #pragma unroll
       for (int a = 0; a < NP; ++a) out[v * KN + eo + a] = dV[v][a];
   } else {
-    const R dt = (R)sc[ins].dt;
+    const R dt = (R)ldc<COH>(&sc[ins].dt);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
         const R vi = Vn[v][a];
         R y = c1 * (vi + dt * dV[v][a]);
-        if (c0 != R(0)) y += c0 * V0e[v][a];
+        if (c0 != R(0)) y += c0 * ldc<COH>(V0e[v] + a);
         dV[v][a] = y;
       }
     if (ph.pos) positivity_limit<DIM, P, R>(dV, ops, ph.h_floor);
