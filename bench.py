@@ -521,6 +521,19 @@ def newton_main(args):
             stream.synchronize()
         st = nk.run(0)
     total_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs))
+    # the same instance with the explicit SSP-RK3 integrator (CFL-limited step),
+    # for simulated time per wall second at the same physics
+    with torch.cuda.stream(stream):
+        sx, _, _ = G.solver_from_case(case, stream=stream)
+        sx.run(5)
+        t0 = sx.sync()["t"]
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sx.advance(200)
+        e1.record(stream)
+        stream.synchronize()
+        explicit_sim_rate = (sx.sync()["t"] - t0) / (e0.elapsed_time(e1) / 1e3)
+        sx.close()
     steps_timed = args.steps * args.inner
     units_per_step = s.K * s.Np * s.nV
     value = whole_job_throughput(units_per_step * args.inner, args.steps, world, total_ms)
@@ -555,6 +568,7 @@ def newton_main(args):
                        "newton_its_per_step": dn / max(1, steps_timed),
                        "krylov_its_per_newton_it": dk / max(1, dn), "newton": kw,
                        "simulated_time_per_second": dt * steps_timed / (total_ms / 1e3),
+                       "explicit_rk3_simulated_time_per_second": explicit_sim_rate,
                        "l2": "flushed (256 MiB write) before each step", "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "alu", "kernel": "residual evaluations (estep, face, volume mode 2, time term)",
                          "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
