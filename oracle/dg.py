@@ -12,7 +12,9 @@ For each element e this evaluates, with the fixed quadrature of refelem.py,
       flux F_bar (Eq. HLLSolver) and the central Q_bar;
   time derivative: <N, dU/dt> = -r_V with U = (h, h u) (Eq. Uterm), i.e.
       M dh/dt = -r_h and M_h du/dt = -r_u - M_u dh/dt, where
-      M_h = <psi, h psi>, M_u = <psi, u psi> (dU/dV of Appendix A).
+      M_h = <psi, h psi>, M_u = <psi, u psi> (dU/dV of Appendix A); in
+      wet/dry mode the explicit stages update the moments <N, U> instead
+      (ssp_rk3_step).
 
 Unknowns are modal coefficients of V = (h, u) and E (Sec. 5).  Exterior
 (neighbour) values at face points are obtained by mapping the physical point
@@ -386,18 +388,64 @@ class Discretization:
 
     def ssp_rk3_step(self, Vh, dt=None):
         """One Shu-Osher SSP-RK3 step (explicit integrator for the
-        benchmark workloads; the paper itself integrates implicitly).  With
-        prm["positivity"] set, every stage result passes through
-        positivity_limit."""
-        lim = self.positivity_limit if self.prm.get("positivity", 0) else (lambda V: V)
+        benchmark workloads; the paper itself integrates implicitly).
+        Without prm["positivity"] the stages are taken on V = (h, u) with
+        dV/dt from rhs (method of lines through dU/dV).  With it (wet/dry
+        fronts) they are taken on the moments <N, U(V)> of U = (h, h u), the
+        quantity whose difference the paper's time term (Eq. WeakForm7)
+        holds: each Euler substep is <N, U(V')> = <N, U(V)> - dt r_V(V), the
+        stage results are the same convex combinations of moments, and V is
+        recovered from the moments by recover_from_moments (depth limited
+        before the velocity is solved for).  The two forms agree to O(dt^2)
+        per step; only the second stays finite where the depth at the start
+        of a stage is zero, since it divides the new momentum by the new
+        depth instead of the momentum change by the old one."""
         if dt is None:
             dt = self.stable_dt(Vh)
+        if self.prm.get("positivity", 0):
+            m0 = self.moments(Vh)
+            V1 = self.recover_from_moments(m0 - dt * self.residual(Vh))
+            V2 = self.recover_from_moments(0.75 * m0 + 0.25 * (self.moments(V1) - dt * self.residual(V1)))
+            V3 = self.recover_from_moments(m0 / 3.0 + 2.0 / 3.0 * (self.moments(V2) - dt * self.residual(V2)))
+            return V3, dt
         k1, _ = self.rhs(Vh)
-        V1 = lim(Vh + dt * k1)
+        V1 = Vh + dt * k1
         k2, _ = self.rhs(V1)
-        V2 = lim(0.75 * Vh + 0.25 * (V1 + dt * k2))
+        V2 = 0.75 * Vh + 0.25 * (V1 + dt * k2)
         k3, _ = self.rhs(V2)
-        return lim(Vh / 3.0 + 2.0 / 3.0 * (V2 + dt * k3)), dt
+        return Vh / 3.0 + 2.0 / 3.0 * (V2 + dt * k3), dt
+
+    def residual(self, Vh):
+        """r_V of Eq. WeakForm51 (without the time term) with E from the E-step."""
+        return self.spatial_residual(Vh, self.e_step(Vh))
+
+    def moments(self, Vh):
+        """<N, U(V)> per element: the test-function moments of the
+        conservative unknowns U = (h, h u_1, ..., h u_d) (Eq. Uterm), with the
+        products h u_j formed at the volume quadrature points; (nV, K, Np)."""
+        Vq = np.einsum("qa,vka->vkq", self.Phi, Vh)
+        m = np.empty_like(Vh)
+        m[0] = np.einsum("kq,qa,kq->ka", self.wJ, self.Phi, Vq[0])
+        for j in range(self.dim):
+            m[1 + j] = np.einsum("kq,qa,kq->ka", self.wJ, self.Phi, Vq[0] * Vq[1 + j])
+        return m
+
+    def recover_from_moments(self, m):
+        """V from moments m = <N, U>: h from M h = m_h; h through the depth
+        limiter (positivity_limit's scaling); u_j from M_h u_j = m_u_j with
+        M_h = <psi, max(h, h_floor) psi> of the limited depth; u = 0 in
+        elements whose mean depth is below h_floor."""
+        V = np.empty_like(m)
+        V[0] = np.linalg.solve(self.M, m[0][..., None])[..., 0]
+        V[0], hbar = self._limit_depth(V[0])
+        hq = np.maximum(np.einsum("qa,ka->kq", self.Phi, V[0]), self.prm["h_floor"])
+        Mh = np.einsum("kq,kq,qa,qb->kab", self.wJ, hq, self.Phi, self.Phi)
+        for j in range(self.dim):
+            V[1 + j] = np.linalg.solve(Mh, m[1 + j][..., None])[..., 0]
+        dry = hbar < self.prm["h_floor"]
+        for j in range(self.dim):
+            V[1 + j][dry] = 0.0
+        return V
 
     # ------------------------------------------------------------ wet/dry (extension)
     def check_points(self, Vh_field):
@@ -421,7 +469,14 @@ class Discretization:
           otherwise:        h unchanged;
         and u = 0 in elements with hbar < h_floor."""
         V = Vh.copy()
-        h = Vh[0]
+        V[0], hbar = self._limit_depth(Vh[0])
+        dry = hbar < self.prm["h_floor"]
+        for j in range(self.dim):
+            V[1 + j] = np.where(dry[:, None], 0.0, Vh[1 + j])
+        return V
+
+    def _limit_depth(self, h):
+        """The depth part of positivity_limit: (limited h, cell averages)."""
         w = self.wJ
         hbar = np.einsum("kq,kq->k", w, np.einsum("qa,ka->kq", self.Phi, h)) / w.sum(axis=1)
         m = self.check_points(h).min(axis=1)
@@ -431,11 +486,7 @@ class Discretization:
         scaled = hbar[:, None] + theta[:, None] * (hn - hbar[:, None])
         hn_new = np.where((hbar <= 0.0)[:, None], 0.0, np.where((m < 0.0)[:, None], scaled, hn))
         changed = (hbar <= 0.0) | (m < 0.0)
-        V[0] = np.where(changed[:, None], self.to_modal(hn_new), h)
-        dry = hbar < self.prm["h_floor"]
-        for j in range(self.dim):
-            V[1 + j] = np.where(dry[:, None], 0.0, Vh[1 + j])
-        return V
+        return np.where(changed[:, None], self.to_modal(hn_new), h), hbar
 
     def total_mass(self, Vh):
         """Sum over elements of the integral of h (compensated summation)."""
