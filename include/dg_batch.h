@@ -3,7 +3,8 @@
  * regularized-Bingham instances advanced together on one GPU.
  *
  * Each instance has its own mesh, order, regularization and parameters
- * (dg_swe.h types).  Instances are grouped by (dimension, order); every group
+ * (dg_swe.h types).  Instances are grouped by (dimension, order, wet/dry mode
+ * dg_swe_params.positivity); every group
  * stores its instances' elements and faces contiguously ([field][element]
  * [node] over the group), so one launch per group and phase (E-step, face
  * flux, volume/lift/mass-solve/update) advances all of them.  Per-instance
@@ -90,6 +91,9 @@ dg_status dg_batch_time_kernels(dg_batch *b, int n_iter, double *ms, int cap);
 
 /* Totals: elements, DOF (elements x nodes x V fields) and groups. */
 dg_status dg_batch_info(const dg_batch *b, int64_t *elements, int64_t *dofs, int32_t *n_groups);
+/* Kernel launches one step enqueues: 11 per group (14 per wet/dry group, whose
+ * stages add a stage kernel after each volume pass), or 1 per group with
+ * dg_batch_set_persistent. */
 int32_t dg_batch_launches_per_step(const dg_batch *b);
 
 /* Selects how a step is enqueued (the default, on = 0: for every (dimension,
@@ -105,7 +109,8 @@ int32_t dg_batch_launches_per_step(const dg_batch *b);
  * gives up latches DG_ERR_TIMEOUT for its instance (reported by the next
  * synchronizing call).  Discards captured graphs.  Returns
  * DG_ERR_UNSUPPORTED for DG_PREC_FP32_TC batches (the persistent step runs
- * the CUDA-core volume pass).  (A launch structure of
+ * the CUDA-core volume pass) and for batches with a wet/dry group (it has no
+ * wet/dry stage).  (A launch structure of
  * this library's explicit integrator; the paper's scheme is implicit.) */
 dg_status dg_batch_set_persistent(dg_batch *b, int on);
 const char *dg_batch_last_error(const dg_batch *b);

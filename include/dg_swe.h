@@ -114,15 +114,25 @@ typedef struct {
   int32_t precision;            /* DG_PREC_*                                             */
   int32_t n_bc;                 /* entries used in bc[] (>= 1)                           */
   dg_swe_bc bc[DG_SWE_MAX_BC];
-  int32_t positivity;           /* 1: depth limiter after every explicit stage (an
-                                   extension: the paper leaves wet/dry fronts to future
-                                   work, Sec. 7).  Per element, with hbar the cell average
-                                   of h and m the minimum of h over the nodes, volume and
-                                   face quadrature points: hbar <= 0 gives h = 0;
-                                   m < 0 < hbar scales h <- hbar + theta (h - hbar),
-                                   theta = hbar / (hbar - m) (Zhang-Shu scaling); the
-                                   velocity is set to 0 where hbar < h_floor.  Keeps
-                                   cell averages.  0: off (the paper's scheme)           */
+  int32_t positivity;           /* 1: wet/dry mode (an extension: the paper leaves wet/dry
+                                   fronts to future work, Sec. 7).  Each explicit stage is
+                                   taken on the moments <N, U> of U = (h, h u), whose
+                                   difference the time term of Eq. WeakForm7 holds:
+                                   <N, U(y)> = c0 <N, U(V0)> + c1 (<N, U(Vs)> - dt r_V(Vs)).
+                                   The new depth passes the depth limiter (per element,
+                                   with hbar the cell average of h and m its minimum over
+                                   the nodes, volume and face quadrature points: hbar <= 0
+                                   gives h = 0; m < 0 < hbar scales h <- hbar + theta
+                                   (h - hbar), theta = hbar / (hbar - m), Zhang-Shu
+                                   scaling; cell averages kept), then the velocity solves
+                                   M_h u = <psi, h u> with M_h = <psi, max(h, h_floor) psi>
+                                   of the limited depth, and u = 0 where hbar < h_floor.
+                                   Runs dam breaks onto dry beds (depth exactly 0), which
+                                   the primitive stages cannot: they divide the momentum
+                                   change by the stage's starting depth.  The stage is
+                                   formed in FP64 (FP32 contexts too) by a separate kernel
+                                   after the volume pass: 14 launches per step instead of
+                                   11.  0: off (stages on V through dU/dV, Appendix A)   */
   double flow_index;            /* n of a Herschel-Bulkley viscous part (an extension; the
                                    paper's introduction cites the law, its scheme is
                                    Bingham): the Newtonian 2 eta (D + tr D I) becomes
@@ -251,7 +261,8 @@ dg_status dg_swe_residual_static(dg_swe_ctx *ctx, const double *V_dev, double *d
 /* Scratch bytes dg_swe_residual_static needs for this context. */
 size_t dg_swe_static_scratch_need(const dg_swe_ctx *ctx);
 
-/* Number of kernel launches one dg_swe_step enqueues (for launch accounting). */
+/* Number of kernel launches one dg_swe_step enqueues (for launch accounting):
+ * 11, or 14 in wet/dry mode (positivity). */
 int32_t dg_swe_launches_per_step(const dg_swe_ctx *ctx);
 
 const char *dg_swe_last_error(const dg_swe_ctx *ctx);

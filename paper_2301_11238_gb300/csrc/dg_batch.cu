@@ -7,6 +7,7 @@
 #include <map>
 #include <memory>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/dg_batch.h"
@@ -39,6 +40,7 @@ struct GroupDrv {
 
 struct Group {
   int dim = 0, p = 0;
+  bool pos = false;  // wet/dry mode (dg_swe_params.positivity) of all its members
   std::vector<int> members;          // global instance ids
   RefOps ops;
   int64_t K = 0, F = 0;
@@ -238,6 +240,18 @@ struct GDrv final : GroupDrv {
   }
   void volume(dg_batch* b, Group& g, int vin, int vout, double c0, double c1, cudaStream_t s) override {
     const int K = (int)g.K, F = (int)g.F;
+    if (g.pos) {
+      // wet/dry group: r_V (mode 2) into the stage's output buffer, or into
+      // stage buffer 1 when the output is V0 (the last stage), then the
+      // conservative stage from it
+      const int rb = vout != 0 ? vout : 1;
+      residual(b, g, vin, rb, s);
+      wetdry_stage_kernel<DIM, P, R, true><<<(K + 127) / 128, 128, 0, s>>>(
+          K, b->at<R>(g.off.V[vin]), b->at<R>(g.off.V[0]), b->at<R>(g.off.V[rb]), b->at<R>(g.off.V[vout]),
+          b->at<R>(g.off.geo), vo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), (R)c0, (R)c1,
+          b->at<DevScalars>(b->off_sc));
+      return;
+    }
     if constexpr (kTcForm) {
       if (tc) {  // the tensor-core form has its own fixed launch shape; the tile setting is not used
         (*tcl)(K, F, b->at<float>(g.off.V[vin]), b->at<float>(g.off.V[0]), b->at<float>(g.off.V[vout]),
@@ -267,6 +281,27 @@ struct GDrv final : GroupDrv {
           b->at<R>(g.off.geo), b->at<int32_t>(g.off.fid),
         b->at<R>(g.off.wflux), vo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), 1, (R)c0, (R)c1,
         b->at<DevScalars>(b->off_sc));
+  }
+  // the volume pass in mode 2 (r_V of V[vin] into V[vout]): the tensor-core
+  // form or the direct kernel (the staged form has no mode 2; a negative
+  // block size is taken by its magnitude)
+  void residual(dg_batch* b, Group& g, int vin, int vout, cudaStream_t s) {
+    const int K = (int)g.K, F = (int)g.F;
+    if constexpr (kTcForm) {
+      if (tc) {
+        (*tcl)(K, F, b->at<float>(g.off.V[vin]), nullptr, b->at<float>(g.off.V[vout]), b->at<float>(g.off.E),
+               g.has_bed ? b->at<float>(g.off.bed) : nullptr, b->at<float>(g.off.geo), b->at<int32_t>(g.off.fid),
+               b->at<float>(g.off.wflux), vo, b->at<float>(g.off.tcimg), Phys<float>{}, ptab(b),
+               b->at<int32_t>(g.off.inst), 2, 0.0f, 0.0f, b->at<DevScalars>(b->off_sc), s);
+        return;
+      }
+    }
+    const int T = g.tile[2] > 0 ? g.tile[2] : -g.tile[2];
+    volume_kernel<DIM, P, R, true><<<(K + T - 1) / T, T, 0, s>>>(
+        K, F, b->at<R>(g.off.V[vin]), nullptr, b->at<R>(g.off.V[vout]), b->at<R>(g.off.E),
+        g.has_bed ? b->at<R>(g.off.bed) : nullptr, g.has_bed ? b->at<R>(g.off.src) : nullptr, b->at<R>(g.off.geo),
+        b->at<int32_t>(g.off.fid), b->at<R>(g.off.wflux), vo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), 2, R(0),
+        R(0), b->at<DevScalars>(b->off_sc));
   }
   void dt(dg_batch* b, Group& g, cudaStream_t s) override {
     const int nblk = (int)g.blk_gid.size(), nm = (int)g.members.size();
@@ -475,7 +510,7 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
   b->n = n;
   b->prec = params[0].precision;
   b->rsize = b->prec == DG_PREC_FP64 ? 8 : 4;
-  std::map<std::pair<int, int>, int> gidx;
+  std::map<std::tuple<int, int, int>, int> gidx;
   b->group_of.assign(n, -1);
   b->local_of.assign(n, -1);
   b->K_of.assign(n, 0);
@@ -501,13 +536,17 @@ dg_status dg_batch_init(int n, const dg_swe_mesh* meshes, const int* orders, con
     b->order.push_back(c->p);
     b->reg.push_back(c->reg);
     b->prm.push_back(params[i]);
-    auto key = std::make_pair(c->dim, c->p);
+    // wet/dry instances form groups of their own: their stages take the
+    // split volume pass (residual, then wetdry_stage_kernel)
+    const int pos = params[i].positivity ? 1 : 0;
+    auto key = std::make_tuple(c->dim, c->p, pos);
     if (!gidx.count(key)) {
       gidx[key] = (int)b->groups.size();
       b->groups.emplace_back();
       Group& g = b->groups.back();
       g.dim = c->dim;
       g.p = c->p;
+      g.pos = pos != 0;
       g.ops = c->ops;
       g.drv = b->prec == DG_PREC_FP64 ? make_gdrv<double>(g.dim, g.p, g.ops, false)
                                       : make_gdrv<float>(g.dim, g.p, g.ops, b->prec == DG_PREC_FP32_TC);
@@ -1026,13 +1065,21 @@ dg_status dg_batch_info(const dg_batch* b, int64_t* elements, int64_t* dofs, int
 }
 
 int32_t dg_batch_launches_per_step(const dg_batch* b) {
-  return b ? (int32_t)((b->persistent ? 1 : 11) * b->groups.size()) : 0;
+  if (!b) return 0;
+  if (b->persistent) return (int32_t)b->groups.size();
+  int32_t n = 0;
+  for (const auto& g : b->groups) n += g.pos ? 14 : 11;  // wet/dry: a stage kernel after each volume pass
+  return n;
 }
 
 dg_status dg_batch_set_persistent(dg_batch* b, int on) {
   if (!b) return DG_ERR_ARG;
   if (on && b->prec == DG_PREC_FP32_TC)
     return bfail(b, DG_ERR_UNSUPPORTED, "the persistent step runs the CUDA-core volume pass; use DG_PREC_FP32");
+  if (on)
+    for (const auto& g : b->groups)
+      if (g.pos)
+        return bfail(b, DG_ERR_UNSUPPORTED, "the persistent step has no wet/dry (positivity) stage");
   b->persistent = on != 0;
   destroy_graphs(b);
   return DG_OK;

@@ -20,6 +20,10 @@ struct Driver {
   virtual void face(dg_swe_ctx* c, const void* V, const void* E, cudaStream_t s) = 0;
   virtual void volume(dg_swe_ctx* c, const void* Vin, const void* V0, void* out, int mode, double c0,
                       double c1, cudaStream_t s) = 0;
+  // wet/dry mode: out = the conservative stage from Vin, V0 and the residual
+  // rbuf that a volume pass in mode 2 wrote (rbuf and V0 may alias out)
+  virtual void wetdry_stage(dg_swe_ctx* c, const void* Vin, const void* V0, const void* rbuf, void* out, double c0,
+                            double c1, cudaStream_t s) = 0;
   virtual void dt_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
   virtual void mass_partial(dg_swe_ctx* c, const void* V, cudaStream_t s) = 0;
   // Face flux and residual-mode volume pass with caller-chosen scratch for

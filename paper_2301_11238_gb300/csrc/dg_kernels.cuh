@@ -52,7 +52,7 @@ struct Phys {
   R hb_n, hb_floor;  // Herschel-Bulkley flow index and rate floor (dg_swe_params)
   int hb;            // 1: power-law viscous part (flow index != 1)
   int reg;
-  int pos;  // depth limiter after every explicit stage (dg_swe_params.positivity)
+  int pos;  // wet/dry mode: conservative stages with the depth limiter (dg_swe_params.positivity)
 };
 
 // One boundary descriptor: per slot (V fields then E fields) a mode
@@ -561,53 +561,163 @@ __global__ void __launch_bounds__(256, face_min_blocks<DIM, P, R>())
                                        bct);
 }
 
-// Depth limiter of one element's new stage values y (nodal), applied when
-// dg_swe_params.positivity is set (an extension for wet/dry fronts; Zhang-Shu
-// scaling of h): with hbar the cell average of h and m its minimum over the
-// nodes, the volume quadrature points and the face quadrature points,
-// hbar <= 0 gives h = 0, m < 0 < hbar gives h <- hbar + theta (h - hbar) with
-// theta = hbar / (hbar - m); the velocity is zeroed where hbar < h_floor.
+// Depth limiter of one element's nodal depths h (FP64), part of the wet/dry
+// stage below (Zhang-Shu scaling of h): with hbar the cell average of h and m
+// its minimum over the nodes, the volume quadrature points and the face
+// quadrature points, hbar <= 0 gives h = 0, m < 0 < hbar gives
+// h <- hbar + theta (h - hbar) with theta = hbar / (hbar - m).  Returns hbar.
 template <int DIM, int P, typename R>
-__device__ __forceinline__ void positivity_limit(R (&y)[Sh<DIM, P>::NV][Sh<DIM, P>::NP], const VolOps<DIM, P, R>& ops,
-                                                 R h_floor) {
+__device__ __forceinline__ double limit_depth(double* h, const VolOps<DIM, P, R>& ops) {
   using S = Sh<DIM, P>;
-  constexpr int NP = S::NP, NQ = S::NQ, NF = S::NF, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV;
-  R hbar = R(0), m = y[0][0];
-#pragma unroll
+  constexpr int NP = S::NP, NQ = S::NQ, NF = S::NF, NFP = S::NFP, NFQ = S::NFQ;
+  double hbar = 0.0, m = h[0];
+#pragma unroll 1
   for (int a = 0; a < NP; ++a) {
-    hbar += ops.wavg[a] * y[0][a];
-    m = fmin(m, y[0][a]);
+    hbar += (double)ops.wavg[a] * h[a];
+    m = fmin(m, h[a]);
   }
 #pragma unroll 1
   for (int q = 0; q < NQ; ++q) {
-    R hq = R(0);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) hq += ops.Vq[q * NP + a] * y[0][a];
+    double hq = 0.0;
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) hq += (double)ops.Vq[q * NP + a] * h[a];
     m = fmin(m, hq);
   }
-#pragma unroll
+#pragma unroll 1
   for (int f = 0; f < NF; ++f)
-#pragma unroll
+#pragma unroll 1
     for (int mq = 0; mq < NFQ; ++mq) {
-      R hf = R(0);
-#pragma unroll
-      for (int k = 0; k < NFP; ++k) hf += ops.LfT[k * NFQ + mq] * y[0][face_node(DIM, P, f, k)];
+      double hf = 0.0;
+#pragma unroll 1
+      for (int k = 0; k < NFP; ++k) hf += (double)ops.LfT[k * NFQ + mq] * h[face_node(DIM, P, f, k)];
       m = fmin(m, hf);
     }
-  if (hbar <= R(0)) {
-#pragma unroll
-    for (int a = 0; a < NP; ++a) y[0][a] = R(0);
-  } else if (m < R(0)) {
-    const R theta = hbar / (hbar - m);
-#pragma unroll
-    for (int a = 0; a < NP; ++a) y[0][a] = hbar + theta * (y[0][a] - hbar);
+  if (hbar <= 0.0) {
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) h[a] = 0.0;
+  } else if (m < 0.0) {
+    const double theta = hbar / (hbar - m);
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) h[a] = hbar + theta * (h[a] - hbar);
   }
-  if (hbar < h_floor) {
+  return hbar;
+}
+
+// One explicit stage of wet/dry mode (dg_swe_params.positivity), taken on the
+// moments <N, U> of the conservative unknowns U = (h, h u), the quantity whose
+// difference the time term of Eq. WeakForm7 holds, instead of on V:
+//   <N, U(y)> = c0 <N, U(V0)> + c1 (<N, U(Vs)> - dt r_V(Vs)).
+// Solved for y (reference scaling, r times 1/J): the depth from M y_h = ...,
+// i.e. y_h = c0 h0 + c1 (hs - dt M^-1 r_h / J); y_h through limit_depth; then
+// M_h y_u = c0 <psi, h0 u0> + c1 (<psi, hs us> - dt r_u / J) with
+// M_h = <psi, max(y_h, h_floor) psi>, the products formed at the volume
+// quadrature points; y_u = 0 where the mean depth is below h_floor.  The
+// primitive stage divides the momentum change by the stage's starting depth,
+// zero in a dry element; this one divides the new momentum by the new depth.
+// FP64 throughout (FP32 contexts too), in loops over per-thread local
+// arrays.  Runs in its own kernel (wetdry_stage_kernel) after the volume pass
+// has written r_V, so the fused volume kernels carry none of it.  Writes y to
+// out (field stride KN, element offset eo).
+template <int DIM, int P, typename R, bool COH = false>
+__device__ __forceinline__ void conservative_stage(const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                                   const R (&r)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                                   const R* const (&V0e)[Sh<DIM, P>::NV], R c0, R c1, double dt,
+                                                   const VolOps<DIM, P, R>& ops, R h_floor, R Jinv, R* out,
+                                                   size_t KN, size_t eo) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NQ = S::NQ, NV = S::NV;
+  double V[NV * NP], V0[NV * NP], rr[NV * NP], y[NV * NP], mom[DIM * NP], Mh[NP * NP], dinv[NP], z[NP];
 #pragma unroll
-    for (int v = 1; v < NV; ++v)
+  for (int v = 0; v < NV; ++v)
 #pragma unroll
-      for (int a = 0; a < NP; ++a) y[v][a] = R(0);
+    for (int a = 0; a < NP; ++a) {
+      V[v * NP + a] = (double)Vn[v][a];
+      V0[v * NP + a] = c0 != R(0) ? (double)ldc<COH>(V0e[v] + a) : 0.0;
+      rr[v * NP + a] = (double)r[v][a];
+    }
+  const double jinv = (double)Jinv, hf = (double)h_floor, a0 = (double)c0, a1 = (double)c1;
+  // depth
+#pragma unroll 1
+  for (int a = 0; a < NP; ++a) {
+    double acc = 0.0;
+#pragma unroll 1
+    for (int b = 0; b < NP; ++b) acc += (double)ops.Minv[a * NP + b] * rr[b];
+    y[a] = a1 * (V[a] - dt * acc * jinv) + a0 * V0[a];
   }
+  const double hbar = limit_depth<DIM, P, R>(y, ops);
+  // momentum moments and M_h of the limited depth
+#pragma unroll 1
+  for (int i = 0; i < DIM * NP; ++i) mom[i] = -a1 * dt * jinv * rr[NP + i];
+#pragma unroll 1
+  for (int i = 0; i < NP * NP; ++i) Mh[i] = 0.0;
+#pragma unroll 1
+  for (int q = 0; q < NQ; ++q) {
+    double hs = 0.0, h0 = 0.0, hy = 0.0, us[DIM], u0[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) us[j] = u0[j] = 0.0;
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) {
+      const double l = (double)ops.Vq[q * NP + a];
+      hs += l * V[a];
+      h0 += l * V0[a];
+      hy += l * y[a];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) {
+        us[j] += l * V[(1 + j) * NP + a];
+        u0[j] += l * V0[(1 + j) * NP + a];
+      }
+    }
+    const double w = (double)ops.wq[q];
+    const double wh = w * fmax(hy, hf);
+    double mq[DIM];
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) mq[j] = w * (a1 * hs * us[j] + a0 * h0 * u0[j]);
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) {
+      const double la = (double)ops.Vq[q * NP + a];
+#pragma unroll
+      for (int j = 0; j < DIM; ++j) mom[j * NP + a] += mq[j] * la;
+      const double t = wh * la;
+#pragma unroll 1
+      for (int b = 0; b <= a; ++b) Mh[a * NP + b] += t * (double)ops.Vq[q * NP + b];
+    }
+  }
+  // Cholesky of M_h (lower triangle, reciprocal diagonal) and the solves
+#pragma unroll 1
+  for (int a = 0; a < NP; ++a) {
+#pragma unroll 1
+    for (int b = 0; b < a; ++b) {
+      double sum = Mh[a * NP + b];
+#pragma unroll 1
+      for (int c = 0; c < b; ++c) sum -= Mh[a * NP + c] * Mh[b * NP + c];
+      Mh[a * NP + b] = sum * dinv[b];
+    }
+    double d = Mh[a * NP + a];
+#pragma unroll 1
+    for (int c = 0; c < a; ++c) d -= Mh[a * NP + c] * Mh[a * NP + c];
+    dinv[a] = 1.0 / sqrt(d);
+  }
+  const bool dry = hbar < hf;
+#pragma unroll 1
+  for (int j = 0; j < DIM; ++j) {
+    double* u = y + (1 + j) * NP;
+#pragma unroll 1
+    for (int a = 0; a < NP; ++a) {
+      double sum = mom[j * NP + a];
+#pragma unroll 1
+      for (int c = 0; c < a; ++c) sum -= Mh[a * NP + c] * z[c];
+      z[a] = sum * dinv[a];
+    }
+#pragma unroll 1
+    for (int a = NP - 1; a >= 0; --a) {
+      double sum = z[a];
+#pragma unroll 1
+      for (int c = a + 1; c < NP; ++c) sum -= Mh[c * NP + a] * u[c];
+      u[a] = dry ? 0.0 : sum * dinv[a];
+    }
+  }
+#pragma unroll 1
+  for (int i = 0; i < NV * NP; ++i) out[(i / NP) * KN + eo + i % NP] = (R)y[i];
 }
 
 // Primitive-variable mass solve of one element (Appendix A, dU/dV):
@@ -1081,7 +1191,6 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
         if (c0 != R(0)) y += c0 * ldc<COH>(V0e[v] + a);
         dV[v][a] = y;
       }
-    if (ph.pos) positivity_limit<DIM, P, R>(dV, ops, ph.h_floor);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
@@ -1124,6 +1233,40 @@ __global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __re
   for (int v = 0; v < NV; ++v) V0e[v] = V0 ? V0 + v * KN + eo : nullptr;
   volume_element<DIM, P, R>(e, K, F, Vn, En, bed ? bed + eo : nullptr, src, V0e, out, geo, fid, wflux, ops, ph, ins, mode,
                             c0, c1, sc, tab);
+}
+
+// Stage update of wet/dry mode, one thread per element: after a volume pass
+// in mode 2 has written the residual r_V of the stage's input state to rbuf,
+// out = the conservative stage (conservative_stage) from Vin, V0 and rbuf.
+// rbuf and V0 may alias out: each thread reads its element's values of all
+// three before it writes.
+template <int DIM, int P, typename R, bool BATCH>
+__global__ void __launch_bounds__(128) wetdry_stage_kernel(int K, const R* __restrict__ Vin, const R* V0,
+                                                           const R* rbuf, R* out, const R* __restrict__ geo,
+                                                           const VolOps<DIM, P, R> ops, const Phys<R> ph0,
+                                                           const Phys<R>* __restrict__ ptab,
+                                                           const int32_t* __restrict__ inst, R c0, R c1,
+                                                           const DevScalars* __restrict__ sc) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NV = S::NV;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  const int ins = BATCH ? inst[e] : 0;
+  const R h_floor = BATCH ? ptab[ins].h_floor : ph0.h_floor;
+  const size_t KN = (size_t)K * NP;
+  const size_t eo = (size_t)e * NP;
+  R Vn[NV][NP], r[NV][NP];
+  const R* V0e[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v) {
+    V0e[v] = V0 + v * KN + eo;
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      Vn[v][a] = Vin[v * KN + eo + a];
+      r[v][a] = rbuf[v * KN + eo + a];
+    }
+  }
+  conservative_stage<DIM, P, R>(Vn, r, V0e, c0, c1, sc[ins].dt, ops, h_floor, geo[6 * K + e], out, KN, eo);
 }
 
 // ------------------------------------------------------------------ backward Euler (Newton-Krylov)

@@ -18,6 +18,7 @@ namespace {
 
 constexpr int kBlock = 128;
 constexpr int kRedBlock = 256;
+constexpr int kWetDryBlock = 128;
 constexpr int kGraphSteps = 16;
 
 inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -138,6 +139,13 @@ struct Impl final : Driver {
         c->at<R>(c->off.geo), c->at<int32_t>(c->off.fid),
         c->at<R>(c->off.wflux), vo, ph, nullptr, nullptr, mode, (R)c0, (R)c1, c->at<DevScalars>(c->off.sc));
   }
+  void wetdry_stage(dg_swe_ctx* c, const void* Vin, const void* V0, const void* rbuf, void* out, double c0,
+                    double c1, cudaStream_t s) override {
+    const int K = (int)c->mesh.K;
+    wetdry_stage_kernel<DIM, P, R, false><<<(K + kWetDryBlock - 1) / kWetDryBlock, kWetDryBlock, 0, s>>>(
+        K, (const R*)Vin, (const R*)V0, (const R*)rbuf, (R*)out, c->at<R>(c->off.geo), vo, ph, nullptr, nullptr,
+        (R)c0, (R)c1, c->at<DevScalars>(c->off.sc));
+  }
   void face_into(dg_swe_ctx* c, const void* V, const void* E, void* wflux, cudaStream_t s) override {
     const int K = (int)c->mesh.K, F = (int)c->mesh.F;
     const long long n = (long long)F * S::NFQ;
@@ -194,11 +202,20 @@ DriverPtr make_driver(const dg_swe_ctx& c) {
 
 cudaStream_t work_stream(dg_swe_ctx* c) { return c->stream; }
 
-void enqueue_stage(dg_swe_ctx* c, const void* Vin, const void* V0, void* Vout, double c0, double c1,
+// One SSP-RK3 stage.  Wet/dry mode (positivity) splits the volume pass: the
+// volume kernel writes r_V (mode 2) to rbuf, a buffer the stage does not
+// otherwise read (its own output, or a free stage buffer when the output is
+// V0), and wetdry_stage_kernel forms the conservative stage from it.
+void enqueue_stage(dg_swe_ctx* c, const void* Vin, const void* V0, void* Vout, void* rbuf, double c0, double c1,
                    cudaStream_t s) {
   c->drv->estep(c, Vin, c->ws + c->off.E, s);
   c->drv->face(c, Vin, c->ws + c->off.E, s);
-  c->drv->volume(c, Vin, V0, Vout, 1, c0, c1, s);
+  if (c->prm.positivity) {
+    c->drv->volume(c, Vin, nullptr, rbuf, 2, 0.0, 0.0, s);
+    c->drv->wetdry_stage(c, Vin, V0, rbuf, Vout, c0, c1, s);
+  } else {
+    c->drv->volume(c, Vin, V0, Vout, 1, c0, c1, s);
+  }
 }
 
 void enqueue_step(dg_swe_ctx* c, double fixed_dt, cudaStream_t s) {
@@ -208,9 +225,9 @@ void enqueue_step(dg_swe_ctx* c, double fixed_dt, cudaStream_t s) {
   c->drv->dt_partial(c, V0, s);
   dt_finalize_kernel<<<1, 256, 0, s>>>(c->nblk_dt, c->at<double>(c->off.partial), fixed_dt,
                                        c->at<DevScalars>(c->off.sc));
-  enqueue_stage(c, V0, V0, V1, 0.0, 1.0, s);
-  enqueue_stage(c, V1, V0, V2, 0.75, 0.25, s);
-  enqueue_stage(c, V2, V0, V0, 1.0 / 3.0, 2.0 / 3.0, s);
+  enqueue_stage(c, V0, V0, V1, V1, 0.0, 1.0, s);
+  enqueue_stage(c, V1, V0, V2, V2, 0.75, 0.25, s);
+  enqueue_stage(c, V2, V0, V0, V1, 1.0 / 3.0, 2.0 / 3.0, s);
 }
 
 void enqueue_mass(dg_swe_ctx* c, int set_ref, cudaStream_t s) {
@@ -672,7 +689,7 @@ dg_status dg_swe_sync(dg_swe_ctx* c, dg_swe_stats* stats) {
   return DG_OK;
 }
 
-int32_t dg_swe_launches_per_step(const dg_swe_ctx* c) { return c ? 11 : 0; }
+int32_t dg_swe_launches_per_step(const dg_swe_ctx* c) { return c ? (c->prm.positivity ? 14 : 11) : 0; }
 
 }  // extern "C"
 

@@ -646,7 +646,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (c0 != 0.0f) y += c0 * V0[v * KN + eo + a];
                 dV[v][a] = y;
               }
-            if (ph.pos) positivity_limit<2, P, float>(dV, ops, ph.h_floor);
 #pragma unroll
             for (int v = 0; v < NV; ++v)
 #pragma unroll
