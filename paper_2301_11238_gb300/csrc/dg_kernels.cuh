@@ -127,12 +127,12 @@ __device__ __forceinline__ float dg_sqrt<float>(float x) {
 
 // Loads of data that another thread block writes during the same launch (the
 // persistent batch kernel, COH = true) go through L2 (ld.global.cg), which is
-// coherent on the GPU; every other kernel (COH = false) loads normally.
-template <bool COH, typename T>
-__device__ __forceinline__ T ldc(const T* p) {
-  if constexpr (COH) return __ldcg(p);
-  else return *p;
-}
+// coherent on the GPU; every other kernel (COH = false) loads normally.  A
+// macro taking base and index, so that the plain loads keep the form
+// base[index] (an index sum added once to the base): the form ptr + a + b
+// through a helper compiled the FP32 kernels to more registers and ran
+// slower (E-step 64 -> 80 registers, 0.36 -> 0.42 ms on 8.4M triangles).
+#define DG_LDC(COH, base, idx) ((COH) ? __ldcg((base) + (idx)) : (base)[idx])
 
 // ------------------------------------------------------------------ physics
 
@@ -326,7 +326,7 @@ __device__ __forceinline__ void estep_element(int e, int K, const R* __restrict_
 #pragma unroll
   for (int j = 0; j < DIM; ++j)
 #pragma unroll
-    for (int a = 0; a < NP; ++a) u[j][a] = ldc<COH>(V + (1 + j) * KN + (size_t)e * NP + a);
+    for (int a = 0; a < NP; ++a) u[j][a] = DG_LDC(COH, V, (1 + j) * KN + (size_t)e * NP + a);
   R G[2][2];
   G[0][0] = geo[e];
   if constexpr (DIM == 2) {
@@ -369,7 +369,7 @@ __device__ __forceinline__ void estep_element(int e, int K, const R* __restrict_
         const int a = face_node(DIM, P, f, k);
         const int b = ops.fmask[f2 * NFP + (NFP - 1 - k)];
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (ldc<COH>(V + (1 + j) * KN + (size_t)e2 * NP + b) - u[j][a]);
+        for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (DG_LDC(COH, V, (1 + j) * KN + (size_t)e2 * NP + b) - u[j][a]);
       }
     } else {
       const BCEntry<R> bc = bct[-1 - e2];
@@ -510,9 +510,9 @@ __device__ __forceinline__ void face_item(long long tid, int K, int F, const R* 
   for (int k = 0; k < NFP; ++k) {
     const size_t a = (size_t)e1 * NP + ops.fmask[f1 * NFP + k];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) Tm[v][k] = ldc<COH>(V + v * KN + a);
+    for (int v = 0; v < NV; ++v) Tm[v][k] = DG_LDC(COH, V, v * KN + a);
 #pragma unroll
-    for (int c = 0; c < NE; ++c) Tm[NV + c][k] = ldc<COH>(E + c * KN + a);
+    for (int c = 0; c < NE; ++c) Tm[NV + c][k] = DG_LDC(COH, E, c * KN + a);
   }
   const bool interior = e2 >= 0;
   if (interior) {
@@ -521,9 +521,9 @@ __device__ __forceinline__ void face_item(long long tid, int K, int F, const R* 
     for (int k = 0; k < NFP; ++k) {
       const size_t b = (size_t)e2 * NP + ops.fmask[f2 * NFP + (NFP - 1 - k)];
 #pragma unroll
-      for (int v = 0; v < NV; ++v) Tp[v][k] = ldc<COH>(V + v * KN + b);
+      for (int v = 0; v < NV; ++v) Tp[v][k] = DG_LDC(COH, V, v * KN + b);
 #pragma unroll
-      for (int c = 0; c < NE; ++c) Tp[NV + c][k] = ldc<COH>(E + c * KN + b);
+      for (int c = 0; c < NE; ++c) Tp[NV + c][k] = DG_LDC(COH, E, c * KN + b);
     }
   } else {
 #pragma unroll
@@ -632,7 +632,7 @@ __device__ __forceinline__ void conservative_stage(const R (&Vn)[Sh<DIM, P>::NV]
 #pragma unroll
     for (int a = 0; a < NP; ++a) {
       V[v * NP + a] = (double)Vn[v][a];
-      V0[v * NP + a] = c0 != R(0) ? (double)ldc<COH>(V0e[v] + a) : 0.0;
+      V0[v * NP + a] = c0 != R(0) ? (double)DG_LDC(COH, V0e[v], a) : 0.0;
       rr[v * NP + a] = (double)r[v][a];
     }
   const double jinv = (double)Jinv, hf = (double)h_floor, a0 = (double)c0, a1 = (double)c1;
@@ -1147,7 +1147,7 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int m = 0; m < NFQ; ++m) {
-        const R x = ldc<COH>(wflux + v * FQ + base + (own ? m : NFQ - 1 - m));
+        const R x = DG_LDC(COH, wflux, v * FQ + base + (own ? m : NFQ - 1 - m));
         fv[v][m] = own ? x : -x;
       }
 #pragma unroll
@@ -1181,14 +1181,14 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 #pragma unroll
       for (int a = 0; a < NP; ++a) out[v * KN + eo + a] = dV[v][a];
   } else {
-    const R dt = (R)ldc<COH>(&sc[ins].dt);
+    const R dt = (R)DG_LDC(COH, &sc[ins].dt, 0);
 #pragma unroll
     for (int v = 0; v < NV; ++v)
 #pragma unroll
       for (int a = 0; a < NP; ++a) {
         const R vi = Vn[v][a];
         R y = c1 * (vi + dt * dV[v][a]);
-        if (c0 != R(0)) y += c0 * ldc<COH>(V0e[v] + a);
+        if (c0 != R(0)) y += c0 * DG_LDC(COH, V0e[v], a);
         dV[v][a] = y;
       }
 #pragma unroll
@@ -1198,9 +1198,19 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
   }
 }
 
+// Register cap of the direct volume kernel: 168 for FP32 at p = 3, the most
+// that keeps three warps on each SM sub-partition (16,384 registers each; the
+// autotuner picks 32-thread blocks for this kernel).  Left to the compiler
+// it took 171 (176 allocated), two warps per sub-partition, and the p = 3
+// bump volume pass ran 0.40 instead of 0.30 ms.  Otherwise no cap.
+template <int DIM, int P, typename R>
+constexpr int volume_max_regs() {
+  return (sizeof(R) == 4 && P == 3) ? 168 : 255;
+}
+
 // One thread per element; nodal values read straight from global memory.
 template <int DIM, int P, typename R, bool BATCH>
-__global__ void __launch_bounds__(256) volume_kernel(int K, int F, const R* __restrict__ Vin,
+__global__ void __launch_bounds__(256) __maxnreg__((volume_max_regs<DIM, P, R>())) volume_kernel(int K, int F, const R* __restrict__ Vin,
                                                      const R* V0, R* out,
                                                      const R* __restrict__ E, const R* __restrict__ bed, const R* __restrict__ src,
                                                      const R* __restrict__ geo, const int32_t* __restrict__ fid,

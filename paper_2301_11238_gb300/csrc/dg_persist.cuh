@@ -159,11 +159,11 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const Plan pl, const Arr
         bool bad = false;
 #pragma unroll
         for (int a = 0; a < NP; ++a) {
-          const R h = ldc<true>(A.V[0] + (size_t)e * NP + a);
+          const R h = DG_LDC(true, A.V[0], (size_t)e * NP + a);
           R sp2 = R(0);
 #pragma unroll
           for (int jj = 0; jj < DIM; ++jj) {
-            const R u = ldc<true>(A.V[0] + (1 + jj) * KN + (size_t)e * NP + a);
+            const R u = DG_LDC(true, A.V[0], (1 + jj) * KN + (size_t)e * NP + a);
             sp2 += u * u;
           }
           const R l = sqrt(sp2) + sqrt((R)gc * fmax(h, (R)h_floor));
@@ -229,9 +229,9 @@ __global__ void __launch_bounds__(kThreads) step_kernel(const Plan pl, const Arr
 #pragma unroll
           for (int a = 0; a < NP; ++a) {
 #pragma unroll
-            for (int v = 0; v < NV; ++v) Vn[v][a] = ldc<true>(A.V[vin] + v * KN + eo2 + a);
+            for (int v = 0; v < NV; ++v) Vn[v][a] = DG_LDC(true, A.V[vin], v * KN + eo2 + a);
 #pragma unroll
-            for (int c = 0; c < NE; ++c) En[c][a] = ldc<true>(A.E + c * KN + eo2 + a);
+            for (int c = 0; c < NE; ++c) En[c][a] = DG_LDC(true, A.E, c * KN + eo2 + a);
           }
           const R* V0e[NV];
 #pragma unroll
