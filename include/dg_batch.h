@@ -64,8 +64,13 @@ dg_status dg_batch_stats(dg_batch *b, dg_swe_stats *stats);
  * thread-block sizes T in {32, 64, 128, 256} on the current state (n_iter
  * launches each, CUDA events) and keeps the fastest.  Kernel forms are
  * encoded in the block-size entry:
+ *   E-step  T > 0: one thread per element; -T: a grid of resident blocks
+ *           whose threads loop over elements, loading the next element's
+ *           face neighbours while computing the current one;
  *   face    T > 0: one thread per edge point;
- *           -T: one thread per face evaluating every edge point;
+ *           -T: one thread per face evaluating every edge point, in a grid
+ *           of resident blocks whose threads loop over faces and load the
+ *           next face's connectivity while computing the current one;
  *   volume  T > 0: one thread per element, nodal values read from global
  *           memory; -T: staged: a persistent grid whose blocks bring the
  *           next tile of T elements into shared memory with bulk

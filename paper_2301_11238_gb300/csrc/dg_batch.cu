@@ -207,6 +207,18 @@ struct GDrv final : GroupDrv {
     staged_grid[T] = nb * n_sm;
     return nb * n_sm;
   }
+  // resident blocks of the grid-stride per-face kernel at block size T, times the SMs
+  std::map<int, int> pf_grid;
+  int face_pf_blocks(int T) {
+    auto it = pf_grid.find(T);
+    if (it != pf_grid.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, face_pf_kernel<DIM, P, R>, T, 0) != cudaSuccess || nb < 1)
+      nb = 1;
+    cudaGetLastError();
+    pf_grid[T] = nb * (n_sm > 0 ? n_sm : 1);
+    return pf_grid[T];
+  }
   bool volume_ok(int tile) override {
     if (tile > 0) return tile >= 32 && tile <= 256 && tile % 32 == 0;
     const int T = -tile;
@@ -216,8 +228,30 @@ struct GDrv final : GroupDrv {
   const Phys<R>* ptab(dg_batch* b) { return b->at<Phys<R>>(b->off_ptab); }
   const BCEntry<R>* bct(dg_batch* b) { return b->at<BCEntry<R>>(b->off_bct); }
 
+  std::map<int, int> estep_grid;
+  int estep_pf_blocks(int T) {
+    auto it = estep_grid.find(T);
+    if (it != estep_grid.end()) return it->second;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, estep_pf_kernel<DIM, P, R>, T, 0) != cudaSuccess || nb < 1)
+      nb = 1;
+    cudaGetLastError();
+    estep_grid[T] = nb * (n_sm > 0 ? n_sm : 1);
+    return estep_grid[T];
+  }
+  // tile[0] > 0: one thread per element; < 0: the grid-stride form that
+  // prefetches the next element's neighbours (|tile| threads per block)
   void estep(dg_batch* b, Group& g, int vin, cudaStream_t s) override {
-    const int K = (int)g.K, T = g.tile[0];
+    const int K = (int)g.K;
+    if (g.tile[0] < 0) {
+      const int T = -g.tile[0];
+      const int grid = std::max(1, std::min((K + T - 1) / T, estep_pf_blocks(T)));
+      estep_pf_kernel<DIM, P, R><<<grid, T, 0, s>>>(
+          K, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<R>(g.off.geo), b->at<int32_t>(g.off.nbr),
+          b->at<int8_t>(g.off.nbrf), b->at<R>(g.off.fn), b->at<R>(g.off.fsj), eo, bct(b));
+      return;
+    }
+    const int T = g.tile[0];
     estep_kernel<DIM, P, R><<<(K + T - 1) / T, T, 0, s>>>(
         K, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<R>(g.off.geo), b->at<int32_t>(g.off.nbr),
         b->at<int8_t>(g.off.nbrf), b->at<R>(g.off.fn), b->at<R>(g.off.fsj), eo, bct(b));
@@ -232,10 +266,13 @@ struct GDrv final : GroupDrv {
           b->at<int32_t>(g.off.fe2), b->at<int8_t>(g.off.ff2), b->at<R>(g.off.fnrm), b->at<R>(g.off.fsjf),
           b->at<R>(g.off.wflux), fo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), bct(b));
     } else {
-      face_kernel<DIM, P, R, true, true><<<(unsigned)((F + T - 1) / T), T, 0, s>>>(
+      // one thread per face in a grid-stride loop over the resident blocks
+      // (the next face's connectivity loads while the current one computes)
+      const int grid = std::max(1, std::min((F + T - 1) / T, face_pf_blocks(T)));
+      face_pf_kernel<DIM, P, R><<<(unsigned)grid, T, 0, s>>>(
           K, F, b->at<R>(g.off.V[vin]), b->at<R>(g.off.E), b->at<int32_t>(g.off.fe1), b->at<int8_t>(g.off.ff1),
           b->at<int32_t>(g.off.fe2), b->at<int8_t>(g.off.ff2), b->at<R>(g.off.fnrm), b->at<R>(g.off.fsjf),
-          b->at<R>(g.off.wflux), fo, Phys<R>{}, ptab(b), b->at<int32_t>(g.off.inst), bct(b));
+          b->at<R>(g.off.wflux), fo, ptab(b), b->at<int32_t>(g.off.inst), bct(b));
     }
   }
   void volume(dg_batch* b, Group& g, int vin, int vout, double c0, double c1, cudaStream_t s) override {
@@ -952,8 +989,9 @@ dg_status dg_batch_autotune(dg_batch* b, int n_iter) {
     for (int k = 0; k < 3; ++k) {
       float best = 1e30f;
       int best_t = g.tile[k];
-      // the face kernel also tries its per-face form, the volume kernel its staged form
-      const int ncand = k == 0 ? 4 : 8;
+      // each kernel also tries its other form (negative block size): the
+      // E-step's grid-stride form, the per-face flux form, the staged volume form
+      const int ncand = 8;
       for (int ci = 0; ci < ncand; ++ci) {
         if (k == 2 && !g.drv->volume_ok(cand[ci])) continue;
         g.tile[k] = cand[ci];
@@ -1036,11 +1074,11 @@ dg_status dg_batch_tiles(const dg_batch* b, int32_t* out, int cap, int32_t* n_gr
 dg_status dg_batch_set_tiles(dg_batch* b, const int32_t* tiles, int n) {
   if (!b || !tiles || n != 3 * (int)b->groups.size()) return bfail(b, DG_ERR_ARG, "need 3 block sizes per group");
   for (int i = 0; i < n; ++i) {
-    const int v = (i % 3 != 0 && tiles[i] < 0) ? -tiles[i] : tiles[i];
+    const int v = tiles[i] < 0 ? -tiles[i] : tiles[i];
     if (v < 32 || v > 256 || v % 32)
       return bfail(b, DG_ERR_ARG,
-                   "block sizes must be 32..256, multiples of 32 (negative face entry: per-face form; negative "
-                   "volume entry: staged form)");
+                   "block sizes must be 32..256, multiples of 32 (negative E-step entry: grid-stride form; negative "
+                   "face entry: per-face form; negative volume entry: staged form)");
     if (i % 3 == 2 && !b->groups[i / 3].drv->volume_ok(tiles[i]))
       return bfail(b, DG_ERR_ARG, "staged volume block size " + std::to_string(v) +
                                       " does not fit in shared memory for this group");

@@ -312,13 +312,16 @@ __device__ __forceinline__ void q_normal(R h, const R* E, const R* n, const Phys
 
 // ------------------------------------------------------------------ kernels
 
-// E-step of element e (the body of estep_kernel).
-template <int DIM, int P, typename R, bool COH = false>
+// E-step of element e (the body of estep_kernel).  PRE: the element's face
+// neighbours and their local faces arrive preloaded in pnb / pnbf (one per
+// face) instead of being read from nbr / nbrf.
+template <int DIM, int P, typename R, bool COH = false, bool PRE = false>
 __device__ __forceinline__ void estep_element(int e, int K, const R* __restrict__ V, R* __restrict__ E,
                                               const R* __restrict__ geo, const int32_t* __restrict__ nbr,
                                               const int8_t* __restrict__ nbrf, const R* __restrict__ fn,
                                               const R* __restrict__ fsj, const EstepOps<DIM, P, R>& ops,
-                                              const BCEntry<R>* __restrict__ bct) {
+                                              const BCEntry<R>* __restrict__ bct, const int* pnb = nullptr,
+                                              const int* pnbf = nullptr) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NF = S::NF, NFP = S::NFP, NE = S::NE;
   const size_t KN = (size_t)K * NP;
@@ -356,14 +359,14 @@ __device__ __forceinline__ void estep_element(int e, int K, const R* __restrict_
   }
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const int e2 = nbr[f * K + e];
+    const int e2 = PRE ? pnb[f] : nbr[f * K + e];
     R n[DIM];
 #pragma unroll
     for (int i = 0; i < DIM; ++i) n[i] = fn[(f * DIM + i) * K + e];
     const R sc = fsj[f * K + e] * Jinv;
     R gj[NFP][DIM];
     if (e2 >= 0) {
-      const int f2 = nbrf[f * K + e];
+      const int f2 = PRE ? pnbf[f] : nbrf[f * K + e];
 #pragma unroll
       for (int k = 0; k < NFP; ++k) {
         const int a = face_node(DIM, P, f, k);
@@ -559,6 +562,144 @@ __global__ void __launch_bounds__(256, face_min_blocks<DIM, P, R>())
   if (tid >= nthreads) return;
   face_item<DIM, P, R, BATCH, PERFACE>(tid, K, F, V, E, fe1, ff1, fe2, ff2, fnrm, fsj, wflux, ops, ph0, ptab, inst,
                                        bct);
+}
+
+// Per-face flux kernel over a grid-stride loop, for batch groups: while a
+// thread gathers and evaluates face fc, the connectivity of its next face
+// (fc + grid size: both elements and local faces, normal, scaled Jacobian)
+// is already on its way, so each face costs one dependent round trip to
+// memory (the trace gathers) instead of two.  Same per-point arithmetic as
+// face_kernel (face_point).  The gather and evaluation below restate
+// face_item's after its connectivity loads, so that face_kernel keeps its
+// own compiled form.
+template <int DIM, int P, typename R>
+__device__ __forceinline__ void face_pf_body(int fc, int e1, int f1, int e2, int f2, const R (&n)[DIM], R wsj,
+                                             int K, int F, const R* __restrict__ V, const R* __restrict__ E,
+                                             R* __restrict__ wflux, const FaceOps<DIM, P, R>& ops,
+                                             const Phys<R>* __restrict__ ptab, const int32_t* __restrict__ inst,
+                                             const BCEntry<R>* __restrict__ bct) {
+  using S = Sh<DIM, P>;
+  constexpr int NP = S::NP, NFP = S::NFP, NFQ = S::NFQ, NV = S::NV, NE = S::NE;
+  const size_t KN = (size_t)K * NP;
+  const Phys<R> ph = ptab[inst[e1]];
+  R Tm[NV + NE][NFP], Tp[NV + NE][NFP];
+#pragma unroll
+  for (int k = 0; k < NFP; ++k) {
+    const size_t a = (size_t)e1 * NP + ops.fmask[f1 * NFP + k];
+#pragma unroll
+    for (int v = 0; v < NV; ++v) Tm[v][k] = V[v * KN + a];
+#pragma unroll
+    for (int c = 0; c < NE; ++c) Tm[NV + c][k] = E[c * KN + a];
+  }
+  const bool interior = e2 >= 0;
+  if (interior) {
+#pragma unroll
+    for (int k = 0; k < NFP; ++k) {
+      const size_t b = (size_t)e2 * NP + ops.fmask[f2 * NFP + (NFP - 1 - k)];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Tp[v][k] = V[v * KN + b];
+#pragma unroll
+      for (int c = 0; c < NE; ++c) Tp[NV + c][k] = E[c * KN + b];
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < NV + NE; ++r)
+#pragma unroll
+      for (int k = 0; k < NFP; ++k) Tp[r][k] = Tm[r][k];
+  }
+  const size_t FQ = (size_t)F * NFQ;
+#pragma unroll
+  for (int m = 0; m < NFQ; ++m)
+    face_point<DIM, P, R>(m, Tm, Tp, interior, bct, -1 - e2, n, wsj, ops, ph, wflux, FQ, (size_t)fc * NFQ + m);
+}
+
+template <int DIM, int P, typename R>
+constexpr int face_pf_min_blocks() {
+  return (sizeof(R) == 4 && P <= 2) ? 2 : 1;
+}
+
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(256, face_pf_min_blocks<DIM, P, R>())
+    face_pf_kernel(int K, int F, const R* __restrict__ V, const R* __restrict__ E, const int32_t* __restrict__ fe1,
+                   const int8_t* __restrict__ ff1, const int32_t* __restrict__ fe2, const int8_t* __restrict__ ff2,
+                   const R* __restrict__ fnrm, const R* __restrict__ fsj, R* __restrict__ wflux,
+                   const FaceOps<DIM, P, R> ops, const Phys<R>* __restrict__ ptab, const int32_t* __restrict__ inst,
+                   const BCEntry<R>* __restrict__ bct) {
+  const int stride = gridDim.x * blockDim.x;
+  int fc = blockIdx.x * blockDim.x + threadIdx.x;
+  if (fc >= F) return;
+  int e1 = fe1[fc], f1 = ff1[fc], e2 = fe2[fc], f2 = ff2[fc];
+  R n[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) n[i] = fnrm[(size_t)i * F + fc];
+  R wsj = fsj[fc];
+  for (;;) {
+    const int nx = fc + stride;
+    const bool more = nx < F && nx > fc;  // (nx > fc: no int overflow past F)
+    int e1n = 0, f1n = 0, e2n = -1, f2n = 0;
+    R nn[DIM], wsjn = R(0);
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) nn[i] = R(0);
+    if (more) {
+      e1n = fe1[nx];
+      f1n = ff1[nx];
+      e2n = fe2[nx];
+      f2n = ff2[nx];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) nn[i] = fnrm[(size_t)i * F + nx];
+      wsjn = fsj[nx];
+    }
+    face_pf_body<DIM, P, R>(fc, e1, f1, e2, f2, n, wsj, K, F, V, E, wflux, ops, ptab, inst, bct);
+    if (!more) break;
+    fc = nx;
+    e1 = e1n;
+    f1 = f1n;
+    e2 = e2n;
+    f2 = f2n;
+#pragma unroll
+    for (int i = 0; i < DIM; ++i) n[i] = nn[i];
+    wsj = wsjn;
+  }
+}
+
+// E-step over a grid-stride loop, for batch groups: the face neighbours (and
+// their local faces) of a thread's next element are loaded while the current
+// element is computed, so the neighbour-trace gathers need no dependent
+// round trip to the connectivity first.  Same arithmetic as estep_kernel.
+template <int DIM, int P, typename R>
+__global__ void __launch_bounds__(256) estep_pf_kernel(int K, const R* __restrict__ V, R* __restrict__ E,
+                                                       const R* __restrict__ geo, const int32_t* __restrict__ nbr,
+                                                       const int8_t* __restrict__ nbrf, const R* __restrict__ fn,
+                                                       const R* __restrict__ fsj, const EstepOps<DIM, P, R> ops,
+                                                       const BCEntry<R>* __restrict__ bct) {
+  constexpr int NF = Sh<DIM, P>::NF;
+  const int stride = gridDim.x * blockDim.x;
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= K) return;
+  int nb[NF], nbf[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    nb[f] = nbr[f * K + e];
+    nbf[f] = nbrf[f * K + e];
+  }
+  for (;;) {
+    const int nx = e + stride;
+    const bool more = nx < K && nx > e;  // (nx > e: no int overflow past K)
+    int nbn[NF], nbfn[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      nbn[f] = more ? nbr[f * K + nx] : 0;
+      nbfn[f] = more ? (int)nbrf[f * K + nx] : 0;
+    }
+    estep_element<DIM, P, R, false, true>(e, K, V, E, geo, nbr, nbrf, fn, fsj, ops, bct, nb, nbf);
+    if (!more) break;
+    e = nx;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      nb[f] = nbn[f];
+      nbf[f] = nbfn[f];
+    }
+  }
 }
 
 // Depth limiter of one element's nodal depths h (FP64), part of the wet/dry

@@ -63,11 +63,11 @@ def test_autotune_keeps_results():
     B1, _ = G.batch_from_cases(cases)
     B2, _ = G.batch_from_cases(cases)
     tiles = B2.autotune(3)
-    # per-face form of the face kernel and staged form of the volume kernel
+    # the grid-stride E-step, the per-face flux and the staged volume forms
     # are reported as negative block sizes
     sizes = (32, 64, 128, 256)
     for g in tiles:
-        assert g[0] in sizes and abs(g[1]) in sizes and abs(g[2]) in sizes
+        assert abs(g[0]) in sizes and abs(g[1]) in sizes and abs(g[2]) in sizes
     B1.run(10)
     B2.run(10)
     for i in range(len(cases)):
@@ -185,3 +185,41 @@ def test_batch_mass_multiblock_instances():
         assert abs(ss["mass0"] - st[i]["mass0"]) <= 1e-14 * abs(ss["mass0"])
         s.close()
     B.close()
+
+
+def _run_with_tiles(cases, precision, tiles_fn, steps):
+    import paper_2301_11238_gb300 as G
+    B, _ = G.batch_from_cases(cases, precision=precision)
+    B.set_tiles([tiles_fn(t) for t in B.tiles()])
+    B.run(steps)
+    out = [B.get_state(i) for i in range(len(cases))]
+    B.close()
+    return out
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_grid_stride_estep_and_face_forms_equal_direct(prec):
+    """The grid-stride E-step (negative E-step block size) and the per-face
+    flux form with connectivity prefetch (negative face block size) do the
+    arithmetic of the direct kernels: FP64 states bitwise equal after 12
+    steps on the mixed 1D/2D groups of every order, and after 3 steps on
+    131,072 triangles, where every thread of the resident grid walks several
+    elements and faces (block sizes 32 and 96 leave ragged ends).  FP32 to
+    1e-9 relative (the compiler may fuse multiply-adds differently)."""
+    cases = _mixed_cases()
+    ref = _run_with_tiles(cases, prec, lambda t: [64, 64, 64], 12)
+    for T in (-32, -64, -256):
+        got = _run_with_tiles(cases, prec, lambda t: [T, T, 64], 12)
+        for i in range(len(cases)):
+            if prec == 0:
+                assert np.array_equal(got[i], ref[i]), (T, i, rel_l2(got[i], ref[i]))
+            else:
+                assert rel_l2(got[i], ref[i]) < 1e-9, (T, i, rel_l2(got[i], ref[i]))
+    big = [synth.radial_dam_2d(n=256, order=2, reg=1, sigma0=0.02)]
+    ref = _run_with_tiles(big, prec, lambda t: [128, 128, 128], 3)[0]
+    for T in (-32, -96, -128):
+        got = _run_with_tiles(big, prec, lambda t: [T, T, 128], 3)[0]
+        if prec == 0:
+            assert np.array_equal(got, ref), (T, rel_l2(got, ref))
+        else:
+            assert rel_l2(got, ref) < 1e-9, (T, rel_l2(got, ref))
