@@ -46,12 +46,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="slump",
-                    choices=["radial", "dam1d", "bump", "ensemble", "slump", "implicit_dam", "newton2d"],
+                    choices=["radial", "dam1d", "bump", "ensemble", "slump", "implicit_dam", "newton2d", "drybed"],
                     help="radial: 9-instance radial dam-break sweep (64x64x2, p=2); dam1d: 1D dam break "
                          "(200 el, p=1); bump: dam break over a bump (512x512x2 jittered, p=3); ensemble: "
                          "256 heterogeneous instances; slump: 2048x2048x2 Bingham slump (p=2); implicit_dam: "
                          "the paper's 1D dam break with backward Euler + Newton (100 el, p=1, m3=0, dt=1e-6); "
-                         "newton2d: 2D radial dam break (64x64x2, p=2) with backward Euler + Newton-Krylov")
+                         "newton2d: 2D radial dam break (64x64x2, p=2) with backward Euler + Newton-Krylov; "
+                         "drybed: 2D dam break onto a dry bed in wet/dry mode (1024x1024x2, p=1)")
     ap.add_argument("--solver", default="mixed", choices=["fp64", "mixed"],
                     help="implicit_dam: FP64 block Thomas, or FP32 factorization + FP64 refinement")
     ap.add_argument("--precision", default=None, choices=["fp64", "fp32", "fp32tc"],
@@ -83,7 +84,7 @@ def parse():
     if a.inner is None:
         a.inner = d["inner"]
     if a.n is None:
-        a.n = {"bump": 512, "slump": 2048}.get(a.workload, 64)
+        a.n = {"bump": 512, "slump": 2048, "drybed": 1024}.get(a.workload, 64)
     return a
 
 
@@ -95,6 +96,7 @@ WORKLOAD_DEFAULTS = {
     "slump": dict(precision="fp64", inner=1),
     "implicit_dam": dict(precision="fp64", inner=200),
     "newton2d": dict(precision="fp64", inner=2),
+    "drybed": dict(precision="fp64", inner=10),
 }
 
 # backward-Euler step of the newton2d workload, in multiples of the explicit
@@ -131,6 +133,8 @@ def workload_cases(args):
         return [synth.paper_dam_break_1d(n_el=100, order=1, m3=0, reg=1, gamma=1e2, beta=1e2)]
     if args.workload == "newton2d":
         return [newton2d_case(args.n, args.order)]
+    if args.workload == "drybed":
+        return [synth.dry_dam_2d(n=args.n)]
     return [synth.slump_2d(n=args.n)]
 
 
@@ -151,6 +155,8 @@ def sample_case(workload, n, order):
     if workload == "newton2d":
         return (newton2d_case(6, order),
                 f"the same physics on a 6x6x2 mesh (p={order}), dt = {NEWTON2D_DT_FACTOR:g} x its explicit bound")
+    if workload == "drybed":
+        return synth.dry_dam_2d(n=32), "dry-bed dam break on a 32x32x2 mesh (p=1, wet/dry mode), same physics"
     if workload == "ensemble":
         c = synth.ensemble_cases(n_inst=8, size_scale=0.1)[1]
         return c, f"one ensemble-style instance ({c.dim}D, p={c.order}, {c.etov.shape[0]} elements)"
@@ -167,6 +173,8 @@ def workload_name(args):
             "slump": f"slump_2d {args.n}x{args.n}x2 triangles, p=2, slope 0.05, 16-mode bed (seed 5), bi-viscosity",
             "implicit_dam": "paper_dam_break_1d 100 elements, p=1, m3=0, backward Euler + Newton, dt=1e-6, "
                             "regularization 1 gamma=beta=1e2",
+            "drybed": f"dry_dam_2d {args.n}x{args.n}x2 triangles on [-1,1]^2, p=1, depth 1 | 0 (dry) at x_1 = 0, "
+                      "Newtonian limit, reflecting walls, wet/dry mode (conservative-moment stages, depth limiter)",
             "newton2d": f"radial_dam_2d {args.n}x{args.n}x2 triangles, p={args.order}, tanh regularization "
                         f"sigma0=0.02 gamma=50 eta=0.01, backward Euler + Newton-Krylov, dt = "
                         f"{NEWTON2D_DT_FACTOR:g} x the explicit bound"}[
@@ -768,6 +776,10 @@ def roofline(r, prec, G, args, peaks_derived, peaks_probe, batch_mode):
     wl_key = f"{args.workload}_{args.mode}_{'fp64' if rs == 8 else ('fp32tc' if tcf else 'fp32')}"
     kname = (f"volume_tc_kernel<{p},{'true' if batch_mode else 'false'}>" if tcf else
              f"volume_kernel<{dim},{p},{'double' if rs == 8 else 'float'},{'true' if batch_mode else 'false'}>")
+    if args.workload == "drybed":
+        # wet/dry mode: the volume pass is the residual (volume kernel, mode 2)
+        # plus the FP64 conservative stage kernel; kernel_ms covers both
+        kname = f"{kname} (residual) + wetdry_stage_kernel<{dim},{p},{'double' if rs == 8 else 'float'}>"
     return {"bound": "alu", "kernel": kname,
             "achieved": achieved_tf, "peak": peak, "unit": "TFLOP/s", "frac": achieved_tf / peak,
             "peak_source": (f"{'FP64' if rs == 8 else 'FP32'} pipe from unit counts: SMs x "

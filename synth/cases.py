@@ -159,6 +159,20 @@ def bump_dam_2d(n=512, order=3, seed=3, sigma0=0.05, eta=0.01, gamma=1e3, amp=0.
                 h_fn=h_fn, u_fn=_zero_u(2), bed_fn=bed, n_steps=n_steps)
 
 
+def dry_dam_2d(n=1024, order=1, hl=1.0, x_dam=0.0, cfl=0.3, **kw):
+    """Dam break onto a dry bed on [-1, 1]^2 (n x n squares, 2 n^2
+    triangles): depth hl for x_1 < x_dam, exactly 0 beyond, at rest, flat
+    bed, Newtonian limit (no yield stress, no viscosity), reflecting walls,
+    wet/dry mode on.  Its x_1 profile follows Ritter's solution until the
+    waves reach the walls."""
+    coords, etov = rect_tri_mesh(n, n)
+    params = default_params(reg=REG_NONE, sigma0=0.0, eta=0.0, cfl=cfl, positivity=1, **kw)
+    K = etov.shape[0]
+    wall = _bc(modes={1: BC_WALL, 2: BC_WALL})
+    return Case("dry_dam_2d", 2, coords, etov, _face_bc_2d(K), [wall], order, params,
+                h_fn=lambda x, xc: np.where(xc[:, 0] < x_dam, hl, 0.0), u_fn=_zero_u(2))
+
+
 def _fourier_bed(seed, n_modes=16, kmax=4 * math.pi, amp=0.05):
     rng = np.random.default_rng(seed)
     ks = []

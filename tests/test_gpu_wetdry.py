@@ -3,8 +3,6 @@ explicit stages on the conservative moments <N, U> with the depth limiter)
 on the GPU against the oracle: dam breaks onto a 1 : 0.03 bed and onto a dry
 bed (Ritter), which the primitive-variable stages cannot run, in 1D and 2D,
 solo and batched, FP64, FP32 and the tensor-core volume pass."""
-import dataclasses
-import math
 
 import numpy as np
 import pytest
@@ -80,9 +78,7 @@ def test_limited_batch_bitwise_equals_solo_and_fp32_close():
 
 
 def _dry_x_dam_2d(n=20, p=1):
-    base = synth.radial_dam_2d(n=n, order=p, reg=0, sigma0=0.0, eta=0.0, positivity=1)
-    return dataclasses.replace(base, h_fn=lambda x, xc: np.where(xc[:, 0] < 0.0, 1.0, 0.0),
-                               bcs=[([0, 2, 2, 0, 0, 0, 0], [0.0] * 7)])
+    return synth.dry_dam_2d(n=n, order=p)
 
 
 def test_ritter_dry_bed_1d_matches_oracle_and_exact():

@@ -6,7 +6,6 @@ bed against the exact solutions.
 The paper treats wet beds only (its dam break is compared with the
 wet-bed solution, Sec. 6.3) and names dry beds as future work (Sec. 7);
 the limiter is the scaling limiter of Zhang and Shu (2010)."""
-import dataclasses
 import math
 
 import numpy as np
@@ -174,10 +173,7 @@ def test_ritter_dry_bed_2d():
     resolution the 1D scheme gives 3e-2), and the transverse momentum below 1 % of the streamwise
     one."""
     T, x0, hl = 0.05, 0.0, 1.0
-    base = synth.radial_dam_2d(n=20, order=1, reg=0, sigma0=0.0, eta=0.0, positivity=1)
-    case = dataclasses.replace(base, h_fn=lambda x, xc: np.where(xc[:, 0] < x0, hl, 0.0),
-                               bcs=[([0, 2, 2, 0, 0, 0, 0], [0.0] * 7)])
-    d, V0, _ = build(case)
+    d, V0, _ = build(synth.dry_dam_2d(n=20, hl=hl, x_dam=x0))
     Vh, mass0, hmin = _run_to(d, d.to_modal(V0), T)
     assert hmin >= -1e-13
     assert abs(d.total_mass(Vh) - mass0) < 1e-13 * mass0
