@@ -702,43 +702,49 @@ __global__ void __launch_bounds__(256) estep_pf_kernel(int K, const R* __restric
   }
 }
 
+// Unroll factor of the wet/dry stage's loops: full below 2D p = 3, none there.
+template <int DIM, int P>
+constexpr int wd_unroll() {
+  return (DIM == 2 && P == 3) ? 1 : 64;
+}
+
 // Depth limiter of one element's nodal depths h (FP64), part of the wet/dry
 // stage below (Zhang-Shu scaling of h): with hbar the cell average of h and m
 // its minimum over the nodes, the volume quadrature points and the face
 // quadrature points, hbar <= 0 gives h = 0, m < 0 < hbar gives
 // h <- hbar + theta (h - hbar) with theta = hbar / (hbar - m).  Returns hbar.
-template <int DIM, int P, typename R>
-__device__ __forceinline__ double limit_depth(double* h, const VolOps<DIM, P, R>& ops) {
+template <int DIM, int P, typename R, typename T>
+__device__ __forceinline__ T limit_depth(T* h, const VolOps<DIM, P, R>& ops) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NQ = S::NQ, NF = S::NF, NFP = S::NFP, NFQ = S::NFQ;
-  double hbar = 0.0, m = h[0];
-#pragma unroll 1
+  T hbar = T(0), m = h[0];
+#pragma unroll (wd_unroll<DIM, P>())
   for (int a = 0; a < NP; ++a) {
-    hbar += (double)ops.wavg[a] * h[a];
+    hbar += (T)ops.wavg[a] * h[a];
     m = fmin(m, h[a]);
   }
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
   for (int q = 0; q < NQ; ++q) {
-    double hq = 0.0;
-#pragma unroll 1
-    for (int a = 0; a < NP; ++a) hq += (double)ops.Vq[q * NP + a] * h[a];
+    T hq = T(0);
+#pragma unroll (wd_unroll<DIM, P>())
+    for (int a = 0; a < NP; ++a) hq += (T)ops.Vq[q * NP + a] * h[a];
     m = fmin(m, hq);
   }
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
   for (int f = 0; f < NF; ++f)
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
     for (int mq = 0; mq < NFQ; ++mq) {
-      double hf = 0.0;
-#pragma unroll 1
-      for (int k = 0; k < NFP; ++k) hf += (double)ops.LfT[k * NFQ + mq] * h[face_node(DIM, P, f, k)];
+      T hf = T(0);
+#pragma unroll (wd_unroll<DIM, P>())
+      for (int k = 0; k < NFP; ++k) hf += (T)ops.LfT[k * NFQ + mq] * h[face_node(DIM, P, f, k)];
       m = fmin(m, hf);
     }
-  if (hbar <= 0.0) {
-#pragma unroll 1
-    for (int a = 0; a < NP; ++a) h[a] = 0.0;
-  } else if (m < 0.0) {
-    const double theta = hbar / (hbar - m);
-#pragma unroll 1
+  if (hbar <= T(0)) {
+#pragma unroll (wd_unroll<DIM, P>())
+    for (int a = 0; a < NP; ++a) h[a] = T(0);
+  } else if (m < T(0)) {
+    const T theta = hbar / (hbar - m);
+#pragma unroll (wd_unroll<DIM, P>())
     for (int a = 0; a < NP; ++a) h[a] = hbar + theta * (h[a] - hbar);
   }
   return hbar;
@@ -755,109 +761,114 @@ __device__ __forceinline__ double limit_depth(double* h, const VolOps<DIM, P, R>
 // quadrature points; y_u = 0 where the mean depth is below h_floor.  The
 // primitive stage divides the momentum change by the stage's starting depth,
 // zero in a dry element; this one divides the new momentum by the new depth.
-// FP64 throughout (FP32 contexts too), in loops over per-thread local
-// arrays.  Runs in its own kernel (wetdry_stage_kernel) after the volume pass
-// has written r_V, so the fused volume kernels carry none of it.  Writes y to
+// Computed in T: FP64 in FP64 contexts and for near-dry elements of FP32
+// contexts, FP32 for their wet elements (wetdry_stage_kernel chooses, as
+// mass_solve_dispatch does for the primitive stages); loops unrolled up to
+// p = 2 (2D p = 3 keeps them rolled: unrolled, its arrays spilled 13 KB per
+// thread).  Runs in its own
+// kernel (wetdry_stage_kernel) after the volume pass has written r_V, so the
+// fused volume kernels carry none of it.  Writes y to
 // out (field stride KN, element offset eo).
-template <int DIM, int P, typename R, bool COH = false>
+template <int DIM, int P, typename R, typename T, bool COH = false>
 __device__ __forceinline__ void conservative_stage(const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
                                                    const R (&r)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
-                                                   const R* const (&V0e)[Sh<DIM, P>::NV], R c0, R c1, double dt,
+                                                   const R* const (&V0e)[Sh<DIM, P>::NV], R c0, R c1, double dt_in,
                                                    const VolOps<DIM, P, R>& ops, R h_floor, R Jinv, R* out,
                                                    size_t KN, size_t eo) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NQ = S::NQ, NV = S::NV;
-  double V[NV * NP], V0[NV * NP], rr[NV * NP], y[NV * NP], mom[DIM * NP], Mh[NP * NP], dinv[NP], z[NP];
-#pragma unroll
+  T V[NV * NP], V0[NV * NP], rr[NV * NP], y[NV * NP], mom[DIM * NP], Mh[NP * NP], dinv[NP], z[NP];
+#pragma unroll (wd_unroll<DIM, P>())
   for (int v = 0; v < NV; ++v)
-#pragma unroll
+#pragma unroll (wd_unroll<DIM, P>())
     for (int a = 0; a < NP; ++a) {
-      V[v * NP + a] = (double)Vn[v][a];
-      V0[v * NP + a] = c0 != R(0) ? (double)DG_LDC(COH, V0e[v], a) : 0.0;
-      rr[v * NP + a] = (double)r[v][a];
+      V[v * NP + a] = (T)Vn[v][a];
+      V0[v * NP + a] = c0 != R(0) ? (T)DG_LDC(COH, V0e[v], a) : T(0);
+      rr[v * NP + a] = (T)r[v][a];
     }
-  const double jinv = (double)Jinv, hf = (double)h_floor, a0 = (double)c0, a1 = (double)c1;
+  const T jinv = (T)Jinv, hf = (T)h_floor, a0 = (T)c0, a1 = (T)c1;
+  const T dt = (T)dt_in;
   // depth
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
   for (int a = 0; a < NP; ++a) {
-    double acc = 0.0;
-#pragma unroll 1
-    for (int b = 0; b < NP; ++b) acc += (double)ops.Minv[a * NP + b] * rr[b];
+    T acc = T(0);
+#pragma unroll (wd_unroll<DIM, P>())
+    for (int b = 0; b < NP; ++b) acc += (T)ops.Minv[a * NP + b] * rr[b];
     y[a] = a1 * (V[a] - dt * acc * jinv) + a0 * V0[a];
   }
-  const double hbar = limit_depth<DIM, P, R>(y, ops);
+  const T hbar = limit_depth<DIM, P, R, T>(y, ops);
   // momentum moments and M_h of the limited depth
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
   for (int i = 0; i < DIM * NP; ++i) mom[i] = -a1 * dt * jinv * rr[NP + i];
-#pragma unroll 1
-  for (int i = 0; i < NP * NP; ++i) Mh[i] = 0.0;
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
+  for (int i = 0; i < NP * NP; ++i) Mh[i] = T(0);
+#pragma unroll (wd_unroll<DIM, P>())
   for (int q = 0; q < NQ; ++q) {
-    double hs = 0.0, h0 = 0.0, hy = 0.0, us[DIM], u0[DIM];
-#pragma unroll
-    for (int j = 0; j < DIM; ++j) us[j] = u0[j] = 0.0;
-#pragma unroll 1
+    T hs = T(0), h0 = T(0), hy = T(0), us[DIM], u0[DIM];
+#pragma unroll (wd_unroll<DIM, P>())
+    for (int j = 0; j < DIM; ++j) us[j] = u0[j] = T(0);
+#pragma unroll (wd_unroll<DIM, P>())
     for (int a = 0; a < NP; ++a) {
-      const double l = (double)ops.Vq[q * NP + a];
+      const T l = (T)ops.Vq[q * NP + a];
       hs += l * V[a];
       h0 += l * V0[a];
       hy += l * y[a];
-#pragma unroll
+#pragma unroll (wd_unroll<DIM, P>())
       for (int j = 0; j < DIM; ++j) {
         us[j] += l * V[(1 + j) * NP + a];
         u0[j] += l * V0[(1 + j) * NP + a];
       }
     }
-    const double w = (double)ops.wq[q];
-    const double wh = w * fmax(hy, hf);
-    double mq[DIM];
-#pragma unroll
+    const T w = (T)ops.wq[q];
+    const T wh = w * fmax(hy, hf);
+    T mq[DIM];
+#pragma unroll (wd_unroll<DIM, P>())
     for (int j = 0; j < DIM; ++j) mq[j] = w * (a1 * hs * us[j] + a0 * h0 * u0[j]);
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
     for (int a = 0; a < NP; ++a) {
-      const double la = (double)ops.Vq[q * NP + a];
-#pragma unroll
+      const T la = (T)ops.Vq[q * NP + a];
+#pragma unroll (wd_unroll<DIM, P>())
       for (int j = 0; j < DIM; ++j) mom[j * NP + a] += mq[j] * la;
-      const double t = wh * la;
-#pragma unroll 1
-      for (int b = 0; b <= a; ++b) Mh[a * NP + b] += t * (double)ops.Vq[q * NP + b];
+      const T t = wh * la;
+#pragma unroll (wd_unroll<DIM, P>())
+      for (int b = 0; b <= a; ++b) Mh[a * NP + b] += t * (T)ops.Vq[q * NP + b];
     }
   }
   // Cholesky of M_h (lower triangle, reciprocal diagonal) and the solves
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
   for (int a = 0; a < NP; ++a) {
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
     for (int b = 0; b < a; ++b) {
-      double sum = Mh[a * NP + b];
-#pragma unroll 1
+      T sum = Mh[a * NP + b];
+#pragma unroll (wd_unroll<DIM, P>())
       for (int c = 0; c < b; ++c) sum -= Mh[a * NP + c] * Mh[b * NP + c];
       Mh[a * NP + b] = sum * dinv[b];
     }
-    double d = Mh[a * NP + a];
-#pragma unroll 1
+    T d = Mh[a * NP + a];
+#pragma unroll (wd_unroll<DIM, P>())
     for (int c = 0; c < a; ++c) d -= Mh[a * NP + c] * Mh[a * NP + c];
-    dinv[a] = 1.0 / sqrt(d);
+    dinv[a] = T(1) / sqrt(d);
   }
   const bool dry = hbar < hf;
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
   for (int j = 0; j < DIM; ++j) {
-    double* u = y + (1 + j) * NP;
-#pragma unroll 1
+    T* u = y + (1 + j) * NP;
+#pragma unroll (wd_unroll<DIM, P>())
     for (int a = 0; a < NP; ++a) {
-      double sum = mom[j * NP + a];
-#pragma unroll 1
+      T sum = mom[j * NP + a];
+#pragma unroll (wd_unroll<DIM, P>())
       for (int c = 0; c < a; ++c) sum -= Mh[a * NP + c] * z[c];
       z[a] = sum * dinv[a];
     }
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
     for (int a = NP - 1; a >= 0; --a) {
-      double sum = z[a];
-#pragma unroll 1
+      T sum = z[a];
+#pragma unroll (wd_unroll<DIM, P>())
       for (int c = a + 1; c < NP; ++c) sum -= Mh[c * NP + a] * u[c];
-      u[a] = dry ? 0.0 : sum * dinv[a];
+      u[a] = dry ? T(0) : sum * dinv[a];
     }
   }
-#pragma unroll 1
+#pragma unroll (wd_unroll<DIM, P>())
   for (int i = 0; i < NV * NP; ++i) out[(i / NP) * KN + eo + i % NP] = (R)y[i];
 }
 
@@ -1403,7 +1414,7 @@ __global__ void __launch_bounds__(128) wetdry_stage_kernel(int K, const R* __res
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= K) return;
   const int ins = BATCH ? inst[e] : 0;
-  const R h_floor = BATCH ? ptab[ins].h_floor : ph0.h_floor;
+  const Phys<R> ph = BATCH ? ptab[ins] : ph0;
   const size_t KN = (size_t)K * NP;
   const size_t eo = (size_t)e * NP;
   R Vn[NV][NP], r[NV][NP];
@@ -1417,7 +1428,40 @@ __global__ void __launch_bounds__(128) wetdry_stage_kernel(int K, const R* __res
       r[v][a] = rbuf[v * KN + eo + a];
     }
   }
-  conservative_stage<DIM, P, R>(Vn, r, V0e, c0, c1, sc[ins].dt, ops, h_floor, geo[6 * K + e], out, KN, eo);
+  // an element that is exactly dry and at rest in the stage's states with a
+  // zero residual (no water reaches it) stays so: the stage below would give
+  // y = 0 too
+  bool still = true;
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      still = still && Vn[v][a] == R(0) && r[v][a] == R(0);
+      if (c0 != R(0)) still = still && V0e[v][a] == R(0);
+    }
+  if (still) {
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+      for (int a = 0; a < NP; ++a) out[v * KN + eo + a] = R(0);
+    return;
+  }
+  const double dt = sc[ins].dt;
+  const R Jinv = geo[6 * K + e];
+  if constexpr (sizeof(R) == 4) {
+    // FP32 context: FP32 unless a nodal depth of the stage's states is below h_dry
+    R hmin = Vn[0][0];
+#pragma unroll
+    for (int a = 0; a < NP; ++a) {
+      hmin = fmin(hmin, Vn[0][a]);
+      if (c0 != R(0)) hmin = fmin(hmin, V0e[0][a]);
+    }
+    if (hmin >= ph.h_dry) {
+      conservative_stage<DIM, P, R, float>(Vn, r, V0e, c0, c1, dt, ops, ph.h_floor, Jinv, out, KN, eo);
+      return;
+    }
+  }
+  conservative_stage<DIM, P, R, double>(Vn, r, V0e, c0, c1, dt, ops, ph.h_floor, Jinv, out, KN, eo);
 }
 
 // ------------------------------------------------------------------ backward Euler (Newton-Krylov)
