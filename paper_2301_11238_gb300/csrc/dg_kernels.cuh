@@ -388,25 +388,50 @@ __device__ __forceinline__ void estep_element(int e, int K, const R* __restrict_
         for (int j = 0; j < DIM; ++j) gj[k][j] = R(0.5) * (Vp[1 + j] - Vm[1 + j]);
       }
     }
-    // the face's jump terms sc n_i [u_j]/2, scaled once per face node
-    R gt[NFP][DIM][DIM];
+    if constexpr (sizeof(R) == 8) {
+      // FP64 (bound by the FP64 pipe): lift each velocity jump once,
+      // w_j(a) = sum_k LIFT_a,fk [u_j]_k / 2, then scale by sc n_i: NP DIM
+      // (NFP + DIM) multiply-adds per face instead of NP NFP DIM DIM
+      R sn[DIM];
 #pragma unroll
-    for (int i = 0; i < DIM; ++i) {
-      const R sn = sc * n[i];
+      for (int i = 0; i < DIM; ++i) sn[i] = sc * n[i];
 #pragma unroll
-      for (int k = 0; k < NFP; ++k)
+      for (int a = 0; a < NP; ++a) {
+        R w[DIM];
 #pragma unroll
-        for (int j = 0; j < DIM; ++j) gt[k][i][j] = sn * gj[k][j];
-    }
+        for (int j = 0; j < DIM; ++j) w[j] = R(0);
 #pragma unroll
-    for (int a = 0; a < NP; ++a) {
+        for (int k = 0; k < NFP; ++k) {
+          const R L = ops.LIFT[a * (NF * NFP) + f * NFP + k];
 #pragma unroll
-      for (int k = 0; k < NFP; ++k) {
-        const R L = ops.LIFT[a * (NF * NFP) + f * NFP + k];
+          for (int j = 0; j < DIM; ++j) w[j] += L * gj[k][j];
+        }
 #pragma unroll
         for (int i = 0; i < DIM; ++i)
 #pragma unroll
-          for (int j = 0; j < DIM; ++j) Eo[DIM * i + j][a] += L * gt[k][i][j];
+          for (int j = 0; j < DIM; ++j) Eo[DIM * i + j][a] += sn[i] * w[j];
+      }
+    } else {
+      // FP32: the face's jump terms sc n_i [u_j]/2, scaled once per face node
+      R gt[NFP][DIM][DIM];
+#pragma unroll
+      for (int i = 0; i < DIM; ++i) {
+        const R sn = sc * n[i];
+#pragma unroll
+        for (int k = 0; k < NFP; ++k)
+#pragma unroll
+          for (int j = 0; j < DIM; ++j) gt[k][i][j] = sn * gj[k][j];
+      }
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+#pragma unroll
+        for (int k = 0; k < NFP; ++k) {
+          const R L = ops.LIFT[a * (NF * NFP) + f * NFP + k];
+#pragma unroll
+          for (int i = 0; i < DIM; ++i)
+#pragma unroll
+            for (int j = 0; j < DIM; ++j) Eo[DIM * i + j][a] += L * gt[k][i][j];
+        }
       }
     }
   }
