@@ -901,11 +901,14 @@ __device__ __forceinline__ void conservative_stage(const R (&Vn)[Sh<DIM, P>::NV]
 // dV = -M(V)^{-1} r, i.e. M dh/dt = -r_h and M_h du/dt = -r_u - M_u dh/dt,
 // with M_h = <psi, max(h, h_floor) psi> and M_u = <psi, u psi> at the volume
 // quadrature points; r in physical scaling, Jinv = 1 / J.
-template <int DIM, int P, typename R>
+// STASH: the depth and velocity at the volume points arrive in Vqs (kept
+// from the volume-integral loop) instead of being interpolated again.
+template <int DIM, int P, typename R, bool STASH = false>
 __device__ __forceinline__ void mass_solve_element(const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
                                                    const R (&r)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
                                                    const VolOps<DIM, P, R>& ops, R h_floor, R Jinv,
-                                                   R (&dV)[Sh<DIM, P>::NV][Sh<DIM, P>::NP]) {
+                                                   R (&dV)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
+                                                   const R (*Vqs)[Sh<DIM, P>::NV] = nullptr) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NQ = S::NQ;
 #pragma unroll
@@ -927,15 +930,23 @@ __device__ __forceinline__ void mass_solve_element(const R (&Vn)[Sh<DIM, P>::NV]
 #pragma unroll 1
   for (int q = 0; q < NQ; ++q) {
     R hq = R(0), hdq = R(0), uq[DIM];
+    if constexpr (STASH) {
+      hq = Vqs[q][0];
 #pragma unroll
-    for (int j = 0; j < DIM; ++j) uq[j] = R(0);
+      for (int j = 0; j < DIM; ++j) uq[j] = Vqs[q][1 + j];
 #pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      const R l = ops.Vq[q * NP + a];
-      hq += l * Vn[0][a];
-      hdq += l * dV[0][a];
+      for (int a = 0; a < NP; ++a) hdq += ops.Vq[q * NP + a] * dV[0][a];
+    } else {
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) uq[j] += l * Vn[1 + j][a];
+      for (int j = 0; j < DIM; ++j) uq[j] = R(0);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        const R l = ops.Vq[q * NP + a];
+        hq += l * Vn[0][a];
+        hdq += l * dV[0][a];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) uq[j] += l * Vn[1 + j][a];
+      }
     }
     const R wh = ops.wq[q] * fmax(hq, h_floor);
     const R wd = ops.wq[q] * hdq;
@@ -1209,6 +1220,10 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 
   const bool has_src = sizeof(R) == 8 && src != nullptr;
   const bool has_bed = sizeof(R) == 4 && bed_e != nullptr;
+  // FP64: the depth and velocity at the volume points, kept for the mass
+  // solve (per-thread local memory; saves its interpolation of them)
+  constexpr bool kStash = sizeof(R) == 8;
+  R Vqs[kStash ? NQ : 1][NV];
   R Hn[NP];
 #pragma unroll
   for (int a = 0; a < NP; ++a) Hn[a] = has_bed ? bed_e[a] : R(0);
@@ -1246,6 +1261,10 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
         if constexpr (DIM == 2) Hs += ops.Dsq[q * NP + a] * Hn[a];
       }
     }
+    }
+    if constexpr (kStash) {
+#pragma unroll
+      for (int v = 0; v < NV; ++v) Vqs[q][v] = Vq[v];
     }
     const R h = Vq[0];
     const R hr = h * ph.rho_inv;
@@ -1349,7 +1368,10 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
 
   // ---- mass solve: M dh/dt = -r_h ; M_h du/dt = -r_u - M_u dh/dt
   R dV[NV][NP];
-  mass_solve_dispatch<DIM, P, R>(Vn, r, ops, ph, geo[6 * K + e], dV);
+  if constexpr (kStash)
+    mass_solve_element<DIM, P, R, true>(Vn, r, ops, ph.h_floor, geo[6 * K + e], dV, Vqs);
+  else
+    mass_solve_dispatch<DIM, P, R>(Vn, r, ops, ph, geo[6 * K + e], dV);
 
   // ---- output
   if (mode == 0) {
