@@ -1221,7 +1221,9 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
   const bool has_src = sizeof(R) == 8 && src != nullptr;
   const bool has_bed = sizeof(R) == 4 && bed_e != nullptr;
   // FP64: the depth and velocity at the volume points, kept for the mass
-  // solve (per-thread local memory; saves its interpolation of them)
+  // solve (per-thread local memory; saves its interpolation of them).  The
+  // FP32 kernels, issue-bound, ran slower with it (8.4M-triangle slump
+  // volume 0.97 -> 1.07 ms) and interpolate again.
   constexpr bool kStash = sizeof(R) == 8;
   R Vqs[kStash ? NQ : 1][NV];
   R Hn[NP];
