@@ -227,8 +227,9 @@ def volume_flops(dim, p, bed=False):
     f += NQ * per_q + NV * NP               # + J scaling
     f += NF * NFP * NV * 2 * NFQ            # lift of face fluxes
     f += 2 * NP * NP + NP                   # dh/dt = -Minv r_h / J
-    per_q2 = 2 * NP * (2 + dim) + NP * (NP + 1) + 2 * NP * dim + 3
-    f += NQ * per_q2                        # M_h and M_u dh/dt
+    per_q2 = 2 * NP + NP * (NP + 1) + 2 * NP * dim + 3
+    f += NQ * per_q2                        # dh/dt at the points, M_h and M_u dh/dt (h and u
+                                            # at the points are the ones interpolated above)
     f += NP ** 3 // 3 + NP * NP             # Cholesky
     f += dim * 2 * NP * NP                  # two triangular solves per component
     f += NV * NP * 5                        # stage update
