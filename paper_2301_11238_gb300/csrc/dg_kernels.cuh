@@ -902,13 +902,21 @@ __device__ __forceinline__ void conservative_stage(const R (&Vn)[Sh<DIM, P>::NV]
 // with M_h = <psi, max(h, h_floor) psi> and M_u = <psi, u psi> at the volume
 // quadrature points; r in physical scaling, Jinv = 1 / J.
 // STASH: the depth and velocity at the volume points arrive in Vqs (kept
-// from the volume-integral loop) instead of being interpolated again.
+// from the volume-integral loop) instead of being interpolated again, and
+// M_h is assembled as sum_q max(h_q, h_floor) (w_q l_a l_b), the products
+// w_q l_a l_b read from pm (mass_products: the shared operator table) or,
+// with pm = nullptr, formed in the same order here.
+template <int DIM, int P, typename R>
+__host__ __device__ constexpr int mass_products_pad() {
+  return (int)(((Sh<DIM, P>::NP * (Sh<DIM, P>::NP + 1) / 2 * sizeof(R) + 15) / 16) * 16 / sizeof(R));
+}
 template <int DIM, int P, typename R, bool STASH = false>
 __device__ __forceinline__ void mass_solve_element(const R (&Vn)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
                                                    const R (&r)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
                                                    const VolOps<DIM, P, R>& ops, R h_floor, R Jinv,
                                                    R (&dV)[Sh<DIM, P>::NV][Sh<DIM, P>::NP],
-                                                   const R (*Vqs)[Sh<DIM, P>::NV] = nullptr) {
+                                                   const R (*Vqs)[Sh<DIM, P>::NV] = nullptr,
+                                                   const R* pm = nullptr) {
   using S = Sh<DIM, P>;
   constexpr int NP = S::NP, NQ = S::NQ;
 #pragma unroll
@@ -948,16 +956,44 @@ __device__ __forceinline__ void mass_solve_element(const R (&Vn)[Sh<DIM, P>::NV]
         for (int j = 0; j < DIM; ++j) uq[j] += l * Vn[1 + j][a];
       }
     }
-    const R wh = ops.wq[q] * fmax(hq, h_floor);
     const R wd = ops.wq[q] * hdq;
+    if constexpr (STASH) {
+      const R hf = fmax(hq, h_floor);
+      constexpr int MPAD = mass_products_pad<DIM, P, R>();
+      R pq[MPAD];
+      if (pm) {
+        const double2* p2 = reinterpret_cast<const double2*>(pm + q * MPAD);
 #pragma unroll
-    for (int a = 0; a < NP; ++a) {
-      const R la = ops.Vq[q * NP + a];
-      const R t = wh * la;
+        for (int c = 0; c < MPAD / 2; ++c) {
+          const double2 v = p2[c];
+          pq[2 * c] = v.x;
+          pq[2 * c + 1] = v.y;
+        }
+      } else {
 #pragma unroll
-      for (int b = 0; b <= a; ++b) Mh[a][b] += t * ops.Vq[q * NP + b];
+        for (int a = 0, i = 0; a < NP; ++a)
 #pragma unroll
-      for (int j = 0; j < DIM; ++j) rhs[j][a] -= wd * uq[j] * la;
+          for (int b = 0; b <= a; ++b, ++i) pq[i] = (ops.wq[q] * ops.Vq[q * NP + a]) * ops.Vq[q * NP + b];
+      }
+#pragma unroll
+      for (int a = 0, i = 0; a < NP; ++a) {
+#pragma unroll
+        for (int b = 0; b <= a; ++b, ++i) Mh[a][b] += hf * pq[i];
+        const R la = ops.Vq[q * NP + a];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) rhs[j][a] -= wd * uq[j] * la;
+      }
+    } else {
+      const R wh = ops.wq[q] * fmax(hq, h_floor);
+#pragma unroll
+      for (int a = 0; a < NP; ++a) {
+        const R la = ops.Vq[q * NP + a];
+        const R t = wh * la;
+#pragma unroll
+        for (int b = 0; b <= a; ++b) Mh[a][b] += t * ops.Vq[q * NP + b];
+#pragma unroll
+        for (int j = 0; j < DIM; ++j) rhs[j][a] -= wd * uq[j] * la;
+      }
     }
   }
   // Cholesky of the reference-scaled M_h (lower triangle); the diagonal is
@@ -1132,13 +1168,16 @@ struct QTab {
   static constexpr int NP = Sh<DIM, P>::NP, NQ = Sh<DIM, P>::NQ, ROWS = 4;
   static constexpr int PAD = (int)(((NP * sizeof(R) + 15) / 16) * 16 / sizeof(R));
   static constexpr bool USED = sizeof(R) == 8 && DIM == 2;
-  static constexpr int SIZE = USED ? NQ * ROWS * PAD : 2;
+  // after the rows: per volume point the mass products w_q l_a l_b (b <= a,
+  // row by row) of the FP64 mass solve, padded to 16 bytes
+  static constexpr int MBASE = NQ * ROWS * PAD, MPAD = mass_products_pad<DIM, P, R>();
+  static constexpr int SIZE = USED ? MBASE + NQ * MPAD : 2;
 };
 template <int DIM, int P, typename R>
 __device__ __forceinline__ void qtab_fill(R* tab, const VolOps<DIM, P, R>& ops) {
   using T = QTab<DIM, P, R>;
   if constexpr (T::USED) {
-    for (int i = threadIdx.x; i < T::SIZE; i += blockDim.x) {
+    for (int i = threadIdx.x; i < T::MBASE; i += blockDim.x) {
       const int q = i / (T::ROWS * T::PAD), k = (i / T::PAD) % T::ROWS, a = i % T::PAD;
       R v = R(0);
       if (a < T::NP) {
@@ -1146,6 +1185,17 @@ __device__ __forceinline__ void qtab_fill(R* tab, const VolOps<DIM, P, R>& ops) 
         v = k == 0 ? ops.Vq[j] : k == 1 ? ops.Wr[j] : k == 2 ? ops.Ws[j] : ops.Wm[j];
       }
       tab[i] = v;
+    }
+    for (int i = threadIdx.x; i < T::NQ * T::MPAD; i += blockDim.x) {
+      const int q = i / T::MPAD, idx = i % T::MPAD;
+      R v = R(0);
+      if (idx < T::NP * (T::NP + 1) / 2) {
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= idx) ++a;
+        const int b = idx - a * (a + 1) / 2;
+        v = (ops.wq[q] * ops.Vq[q * T::NP + a]) * ops.Vq[q * T::NP + b];
+      }
+      tab[T::MBASE + i] = v;
     }
   }
 }
@@ -1371,7 +1421,8 @@ __device__ __forceinline__ void volume_element(int e, int K, int F, const R (&Vn
   // ---- mass solve: M dh/dt = -r_h ; M_h du/dt = -r_u - M_u dh/dt
   R dV[NV][NP];
   if constexpr (kStash)
-    mass_solve_element<DIM, P, R, true>(Vn, r, ops, ph.h_floor, geo[6 * K + e], dV, Vqs);
+    mass_solve_element<DIM, P, R, true>(Vn, r, ops, ph.h_floor, geo[6 * K + e], dV, Vqs,
+                                        (QTab<DIM, P, R>::USED && tab) ? tab + QTab<DIM, P, R>::MBASE : nullptr);
   else
     mass_solve_dispatch<DIM, P, R>(Vn, r, ops, ph, geo[6 * K + e], dV);
 
