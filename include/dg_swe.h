@@ -130,9 +130,11 @@ typedef struct {
                                    Runs dam breaks onto dry beds (depth exactly 0), which
                                    the primitive stages cannot: they divide the momentum
                                    change by the stage's starting depth.  The stage is
-                                   formed in FP64 (FP32 contexts too) by a separate kernel
-                                   after the volume pass: 14 launches per step instead of
-                                   11.  0: off (stages on V through dU/dV, Appendix A)   */
+                                   formed by a separate kernel after the volume pass (14
+                                   launches per step instead of 11), in FP64, or in FP32
+                                   for the elements of an FP32 context whose nodal depths
+                                   are all at least 1000 h_floor; elements exactly dry
+                                   and at rest with a zero residual stay so.  0: off (stages on V through dU/dV, Appendix A)   */
   double flow_index;            /* n of a Herschel-Bulkley viscous part (an extension; the
                                    paper's introduction cites the law, its scheme is
                                    Bingham): the Newtonian 2 eta (D + tr D I) becomes
