@@ -733,8 +733,8 @@ constexpr int wd_unroll() {
   return (DIM == 2 && P == 3) ? 1 : 64;
 }
 
-// Depth limiter of one element's nodal depths h (FP64), part of the wet/dry
-// stage below (Zhang-Shu scaling of h): with hbar the cell average of h and m
+// Depth limiter of one element's nodal depths h (in the stage's compute type
+// T), part of the wet/dry stage below (Zhang-Shu scaling of h): with hbar the cell average of h and m
 // its minimum over the nodes, the volume quadrature points and the face
 // quadrature points, hbar <= 0 gives h = 0, m < 0 < hbar gives
 // h <- hbar + theta (h - hbar) with theta = hbar / (hbar - m).  Returns hbar.
